@@ -1,0 +1,63 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case compiles a copy of the oracle with ONE planted error (a flipped sign,
+a wrong index or width, a dropped factor, a transposed operand) into a temporary
+directory, runs the pin suite against it in a subprocess, and requires that the
+suite fails.  Nothing here touches the real oracle library or a GPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ram_oracle.c")
+
+MUTANTS = {
+    "ppm_w2_sign": ("double w2 = -h0 * (hm + h0)", "double w2 = h0 * (hm + h0)"),
+    "ppm_dq_width": ("(2.0 * a + b) / (b + c)", "(2.0 * a + b) / (a + c)"),
+    "ppm_face_weight": ("h0 / (h0 + h1) * (q[ip] - q[i])", "h1 / (h0 + h1) * (q[ip] - q[i])"),
+    "ppm_constraint_operand": ("L = 3.0 * Q - 2.0 * R;", "L = 3.0 * Q - 2.0 * L;"),
+    "ppm_q6_sign": ("6.0 * Q - 3.0 * (L + R)", "6.0 * Q - 3.0 * (L - R)"),
+    "ppm_dq_limiter_factor": ("if (2.0 * fabs(dn) < m) m = 2.0 * fabs(dn);",
+                              "if (fabs(dn) < m) m = fabs(dn);"),
+    "plm_harmonic_factor": ("2.0 * dl * dr / (dl + dr)", "dl * dr / (dl + dr)"),
+    "plm_centred_index": ("sigma[i] = (q[ip] - q[im]) / (hl + hr);",
+                          "sigma[i] = (q[ip] - q[i]) / (hl + hr);"),
+    "plm_cumulative_sign": ("0.5 * r->c1[i] * (d * d - d * h)",
+                            "0.5 * r->c1[i] * (d * d + d * h)"),
+    "ppm_cumulative_term": ("S * (0.5 * xi * xi - xi * xi * xi / 3.0));",
+                            "S * (0.5 * xi * xi - xi * xi * xi / 2.0));"),
+    "quartic_degree": ("int lo = side, hi = side + 4;", "int lo = side, hi = side + 3;"),
+    "seam_whole_count": ("c->nwhole = pr - pl - 1 + n;", "c->nwhole = pr - pl + n;"),
+    "tie_to_left_cell": ("if (x[mid] <= y)", "if (x[mid] < y)"),
+    "shift_direction": ("double yy = x[j] - sred;", "double yy = x[j] + sred;"),
+    "no_copy_rule": ("c->copy = (dl == 0.0", "c->copy = (dl == 1.0"),
+    "vanleer_midpoint_sign": ("qhat += sigma[jm] * 0.5 * (dx[jm] - c);",
+                              "qhat += sigma[jm] * 0.5 * (dx[jm] + c);"),
+    "residual_flux_index": ("q_next[i] = q[i] - (flux[cyc(i + 1, n)] - flux[i]) / dx[i];",
+                            "q_next[i] = q[i] - (flux[cyc(i + 1, n)] - flux[i]) / dx[cyc(i + 1, n)];"),
+    "adjoint_quartic_mass": ("gm[cyc(i - 1, n)] += w * (-b[0] - b[1]);",
+                             "gm[cyc(i - 1, n)] += w * (-b[1]);"),
+    "adjoint_upwind_side": ("int up = (c >= 0.0) ? cyc(j - 1, n) : j;",
+                            "int up = (c >= 0.0) ? j : cyc(j - 1, n);"),
+    "adjoint_plm_transpose": ("g_in[ip] += l1[i] / span;", "g_in[ip] -= l1[i] / span;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, "mutation anchor missing: %s" % name
+    mutated = tmp_path / "ram_oracle_mutant.c"
+    mutated.write_text(src.replace(old, new, 1))  # first occurrence: the forward map
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", str(lib),
+                    str(mutated), "-lm"], check=True)
+    env = dict(os.environ, RAM_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "planted mistake %s was not caught:\n%s" % (name, r.stdout[-2000:])

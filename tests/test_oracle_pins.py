@@ -1,0 +1,544 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests re-types the oracle's formulas.  Each checks a property
+that a plausible mistake in the oracle (a dropped term, a wrong sign or index,
+a transposed operand, a mishandled periodic seam) would break:
+
+  conservation (Eq. 10), constants, exact rolls and full-period identity
+  (Sec. 1, Eq. 8), polynomial reproduction, measured convergence order,
+  brute-force quadrature of the reconstructed profile (Eqs. 15-18),
+  textbook PPM interface values (App. A / Colella & Woodward 1984),
+  no new extrema (Sec. 2, Sec. 3.1), the small-shift equivalence with the
+  upwind step (Sec. 3.2), the worked example of Fig. 1, and the transpose
+  identities of the linear step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_05362_gb300 import workloads as wl
+
+EPS = np.finfo(np.float64).eps
+
+
+def rel_l1(a, b, x=None):
+    w = np.ones(len(a)) if x is None else np.diff(x)
+    return float(np.sum(np.abs(a - b) * w) / np.sum(np.abs(b) * w))
+
+
+# ---------------------------------------------------------------------------
+# conservation, constants, rolls
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order,limiter", [(2, True), (2, False), (3, True),
+                                           (3, False), (4, False)])
+@pytest.mark.parametrize("s", [0.0, 1e-3, 0.37, -2.71, 5.0, 123.456])
+def test_mass_conservation(order, limiter, s):
+    """Eq. 10: the remap conserves the total mass to round-off."""
+    x = wl.random_nodes(97, seed=11)
+    q = 1.0 + np.random.default_rng(3).random(97)
+    out = oracle.shift(x, q, s, order, limiter)
+    m0, m1 = oracle.mass(x, q), oracle.mass(x, out)
+    assert abs(m1 - m0) <= 64 * EPS * m0
+
+
+@pytest.mark.parametrize("order,limiter", [(2, True), (3, True), (3, False), (4, False)])
+def test_constant_field(order, limiter):
+    """A constant stays constant.  The only error is the rounding of the shifted
+    edge positions (~eps * L absolute) relative to the smallest width."""
+    x = wl.random_nodes(128, seed=5)
+    c = 3.7
+    out = oracle.shift(x, np.full(128, c), 0.4321, order, limiter)
+    bound = 8 * EPS * (x[-1] - x[0]) / np.diff(x).min()
+    assert np.max(np.abs(out - c)) <= c * bound
+
+
+@pytest.mark.parametrize("order,limiter", [(2, True), (3, True), (3, False), (4, False)])
+@pytest.mark.parametrize("k", [0, 1, 3, 100, 255, 256, 700, -5])
+def test_integer_roll_bit_exact(order, limiter, k):
+    """Sec. 1 (Eq. 8): a whole-cell shift on a uniform periodic mesh is a cyclic
+    permutation with no numerical error (dyadic mesh, so the shifted edges are
+    exact)."""
+    n = 256
+    x = wl.uniform_nodes(n)
+    q = np.random.default_rng(7).random(n)
+    out = oracle.shift(x, q, k / n, order, limiter)
+    assert np.array_equal(out, np.roll(q, k))
+
+
+@pytest.mark.parametrize("m", [1, 2, -3])
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_full_period_identity(m, order):
+    """A shift by whole periods returns the input bit for bit, on any mesh."""
+    x = wl.random_nodes(200, seed=2, x0=-0.3)
+    q = wl.three_gaussians(x, 3)
+    L = x[-1] - x[0]
+    out = oracle.shift(x, q, m * L, order, order != 4)
+    assert np.array_equal(out, q)
+
+
+def test_config_line_uniform_period_recovery():
+    """The uniform 256-cell line: 7.3 cells/step for 2560 steps is 73 periods;
+    with a whole-period total the profile returns close to the input, the mass
+    is conserved and the top-hat stays within its bounds (limited PLM)."""
+    w = wl.line_uniform()
+    x = w.row_nodes(0)
+    q = w.q0.copy()
+    s = oracle.shift_from_velocity(w.v0[0], w.dt)
+    for _ in range(w.steps):
+        q = oracle.step(x, q, s, 2, True)
+    m0 = oracle.mass(x, w.q0)
+    assert abs(oracle.mass(x, q) - m0) <= 1e-13 * m0
+    assert q.min() >= w.q0.min() - 1e-12 and q.max() <= w.q0.max() + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# accuracy: polynomials and convergence order
+# ---------------------------------------------------------------------------
+
+def poly_cell_averages(P, a, b):
+    Pi = P.integ()
+    return (Pi(b) - Pi(a)) / (b - a)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_polynomial_reproduction(order):
+    """Limiter off, cell averages of a polynomial of degree < p: the shifted cell
+    averages are exact to round-off (cells whose stencils touch the seam of the
+    non-periodic polynomial are excluded)."""
+    n = 300
+    x = wl.random_nodes(n, seed=21)
+    rng = np.random.default_rng(22)
+    P = np.polynomial.Polynomial(rng.uniform(-1, 1, order))  # degree order-1
+    q = poly_cell_averages(P, x[:-1], x[1:])
+    s = 7.77 / n
+    out = oracle.shift(x, q, s, order, False)
+    lo, hi = x[:-1] - s, x[1:] - s
+    keep = (lo >= x[4]) & (hi <= x[n - 4])
+    exact = poly_cell_averages(P, lo[keep], hi[keep])
+    assert keep.sum() > 250
+    np.testing.assert_allclose(out[keep], exact, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_linear_profile_kept_with_limiter(order):
+    """A linear profile is not touched by the limiters (no extremum, no clipping)."""
+    n = 200
+    x = wl.random_nodes(n, seed=4)
+    P = np.polynomial.Polynomial([0.3, 2.0])
+    q = poly_cell_averages(P, x[:-1], x[1:])
+    s = 3.3 / n
+    out = oracle.shift(x, q, s, order, True)
+    lo, hi = x[:-1] - s, x[1:] - s
+    keep = (lo >= x[4]) & (hi <= x[n - 4])
+    # rounding of the shifted edges: ~eps * L absolute, relative to the width
+    tol = 8 * EPS * (x[-1] - x[0]) / np.diff(x).min() * np.abs(q).max()
+    np.testing.assert_allclose(out[keep], poly_cell_averages(P, lo[keep], hi[keep]),
+                               rtol=0, atol=tol)
+
+
+def _sine_period_error(n, order, limiter, cells_per_step=7.3):
+    x = wl.uniform_nodes(n)
+    q0 = wl.sine_averages(x)
+    steps = int(round(n / cells_per_step))
+    assert abs(steps * cells_per_step - n) < 1e-9  # same sub-cell fraction at every n
+    s = 1.0 / steps
+    q = q0.copy()
+    for _ in range(steps):
+        q = oracle.shift(x, q, s, order, limiter)
+    return rel_l1(q, q0, x)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_convergence_order_smooth_sine(order):
+    """Limiter off, exact initial cell averages, one period at 7.3 cells/step:
+    the measured order equals the interpolation order p.  N is a multiple of 73 so
+    that every resolution takes the same sub-cell fraction per step."""
+    ns = [146, 292, 584, 1168]
+    errs = [_sine_period_error(n, order, False) for n in ns]
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert abs(-slope - order) < 0.15, (errs, slope)
+
+
+# ---------------------------------------------------------------------------
+# brute-force quadrature of the reconstructed profile (Eqs. 15-18)
+# ---------------------------------------------------------------------------
+
+GL_X, GL_W = np.polynomial.legendre.leggauss(6)
+
+
+def _q_eval(coef, order, x, i, xx):
+    """Evaluate q_i at points xx from the oracle's per-cell coefficients."""
+    a, b = x[i], x[i + 1]
+    h = b - a
+    if order == 2:
+        return coef[i, 0] + coef[i, 1] * (xx - 0.5 * (a + b))
+    xi = (xx - a) / h
+    L, R, S = coef[i]
+    return L + xi * (R - L) + S * xi * (1.0 - xi)
+
+
+def _brute_shift(x, q, s, order, limiter):
+    n = q.size
+    L = x[-1] - x[0]
+    coef = oracle.reconstruct(x, q, order, limiter)
+    out = np.empty(n)
+    for i in range(n):
+        lo, hi = x[i] - s, x[i + 1] - s
+        k0 = math.floor((lo - x[0]) / L) - 1
+        k1 = math.floor((hi - x[0]) / L) + 1
+        brk = [lo, hi]
+        for k in range(k0, k1 + 1):
+            pts = x[:-1] + k * L
+            brk += list(pts[(pts > lo) & (pts < hi)])
+        brk = np.sort(np.array(brk))
+        tot = 0.0
+        for a, b in zip(brk[:-1], brk[1:]):
+            if b <= a:
+                continue
+            mid = 0.5 * (a + b)
+            k = math.floor((mid - x[0]) / L)
+            p = int(np.searchsorted(x, mid - k * L, side="right") - 1)
+            p = min(max(p, 0), n - 1)
+            xx = 0.5 * (b - a) * GL_X + 0.5 * (a + b) - k * L
+            tot += 0.5 * (b - a) * np.dot(GL_W, _q_eval(coef, order, x, p, xx))
+        out[i] = tot / (x[i + 1] - x[i])
+    return out
+
+
+@pytest.mark.parametrize("order,limiter", [(2, True), (2, False), (3, True), (3, False)])
+@pytest.mark.parametrize("s", [0.0123, 0.4, 1.77, -0.91, 3.0 + 1e-9])
+def test_brute_force_quadrature(order, limiter, s):
+    n = 37
+    x = wl.random_nodes(n, seed=31, x0=-0.5)
+    q = 1.0 + np.random.default_rng(32).random(n)
+    out = oracle.shift(x, q, s, order, limiter)
+    ref = _brute_shift(x, q, s, order, limiter)
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-13)
+
+
+def _quartic_pair_G(x, m, i):
+    """G_i for order 4 built independently: numpy fits of the two quartics of the
+    cumulative mass through nodes {i-5/2..i+3/2} and {i-3/2..i+5/2}."""
+    n = m.size
+    L = x[-1] - x[0]
+    idx = np.arange(i - 2, i + 4)            # node indices i-5/2 .. i+5/2 as x[j]
+    pos = np.array([x[j % n] + (j // n) * L for j in idx]) - x[i]
+    cum = np.concatenate([[0.0], np.cumsum(m)])
+    tot = cum[-1]
+    vals = np.array([cum[j % n] + (j // n) * tot for j in idx]) - cum[i]
+    scale = x[i + 1] - x[i]
+    p1 = np.polynomial.Polynomial.fit(pos[:5] / scale, vals[:5], 4, domain=[-1, 1],
+                                      window=[-1, 1])
+    p2 = np.polynomial.Polynomial.fit(pos[1:] / scale, vals[1:], 4, domain=[-1, 1],
+                                      window=[-1, 1])
+    return lambda d: 0.5 * (p1(d / scale) + p2(d / scale))
+
+
+@pytest.mark.parametrize("s", [0.0123, 0.4, -0.91, 2.5])
+def test_brute_force_order4(s):
+    n = 29
+    x = wl.random_nodes(n, seed=41)
+    q = 1.0 + np.random.default_rng(42).random(n)
+    m = q * np.diff(x)
+    out = oracle.shift(x, q, s, 4, False)
+    L = x[-1] - x[0]
+    G = [_quartic_pair_G(x, m, i) for i in range(n)]
+    ref = np.empty(n)
+    for i in range(n):
+        lo, hi = x[i] - s, x[i + 1] - s
+        brk = [lo, hi]
+        for k in range(math.floor((lo - x[0]) / L) - 1, math.floor((hi - x[0]) / L) + 2):
+            pts = x[:-1] + k * L
+            brk += list(pts[(pts > lo) & (pts < hi)])
+        brk = np.sort(brk)
+        tot = 0.0
+        for a, b in zip(brk[:-1], brk[1:]):
+            mid = 0.5 * (a + b)
+            k = math.floor((mid - x[0]) / L)
+            p = int(np.searchsorted(x, mid - k * L, side="right") - 1)
+            base = x[p] + k * L
+            tot += G[p](b - base) - G[p](a - base)
+        ref[i] = tot / (x[i + 1] - x[i])
+    np.testing.assert_allclose(out, ref, rtol=1e-10, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# reconstruction: textbook values and monotonicity
+# ---------------------------------------------------------------------------
+
+def test_ppm_uniform_interface_textbook():
+    """Uniform mesh, limiter off: <Q>_{i+1/2} = 7/12 (Q_i + Q_{i+1}) - 1/12 (Q_{i-1} +
+    Q_{i+2}) (Colella & Woodward 1984, uniform form of App. A)."""
+    n = 50
+    x = wl.uniform_nodes(n)
+    q = np.random.default_rng(8).random(n)
+    c = oracle.reconstruct(x, q, 3, False)
+    qr = c[:, 1]
+    ref = 7 / 12 * (q + np.roll(q, -1)) - 1 / 12 * (np.roll(q, 1) + np.roll(q, -2))
+    np.testing.assert_allclose(qr, ref, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(c[:, 0], np.roll(qr, 1), rtol=0, atol=0)
+
+
+def test_ppm_cubic_interface_exact_nonuniform():
+    """App. A with sums of widths: for cell averages of a cubic the interface value
+    is the cubic's value at the node, on a non-uniform mesh.  (With the printed
+    products the error is O(1), which pins that reading.)"""
+    n = 80
+    x = wl.random_nodes(n, seed=9)
+    P = np.polynomial.Polynomial([0.2, -1.0, 3.0, -2.5])
+    q = poly_cell_averages(P, x[:-1], x[1:])
+    c = oracle.reconstruct(x, q, 3, False)
+    inner = slice(3, n - 4)
+    np.testing.assert_allclose(c[inner, 1], P(x[1:][inner]), rtol=0, atol=1e-12)
+
+
+def test_plm_van_leer_cases():
+    """Sec. 3.1: zero slope at an extremum, harmonic mean of the one-sided slopes
+    otherwise."""
+    x = wl.uniform_nodes(4)        # h = 1/4
+    q = np.array([0.0, 1.0, 3.0, 1.0])
+    c = oracle.reconstruct(x, q, 2, True)
+    h = 0.25
+    dl, dr = (1.0 - 0.0) / h, (3.0 - 1.0) / h
+    assert c[1, 1] == pytest.approx(2 * dl * dr / (dl + dr), rel=1e-15)
+    assert c[2, 1] == 0.0           # cell 2 is a maximum
+    assert c[0, 1] == 0.0           # cell 0 is a minimum (periodic neighbour 1.0)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_no_new_extrema_in_reconstruction(order):
+    """Sec. 2: the limited q_i stays within the range of Q_{i-1}, Q_i, Q_{i+1}.
+    PLM is checked on a uniform mesh: with slopes per unit length the harmonic
+    mean of Sec. 3.1 can overshoot a neighbour on a strongly non-uniform mesh
+    (a property of the stated limiter, recorded with the readings)."""
+    n = 300
+    x = wl.uniform_nodes(n) if order == 2 else wl.random_nodes(n, seed=12)
+    rng = np.random.default_rng(13)
+    q = np.where(rng.random(n) < 0.2, 1.0, 0.0) + 0.1 * rng.random(n)
+    c = oracle.reconstruct(x, q, order, True)
+    lo = np.minimum(np.minimum(np.roll(q, 1), q), np.roll(q, -1))
+    hi = np.maximum(np.maximum(np.roll(q, 1), q), np.roll(q, -1))
+    for i in range(n):
+        xx = np.linspace(x[i], x[i + 1], 33)
+        v = _q_eval(c, order, x, i, xx)
+        assert v.min() >= lo[i] - 1e-13 and v.max() <= hi[i] + 1e-13
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_no_new_extrema_after_shift(order):
+    n = 256
+    x = wl.uniform_nodes(n) if order == 2 else wl.random_nodes(n, seed=14)
+    q = wl.tophat_averages(x, 0.3, 0.55) + 0.25
+    out = q
+    for _ in range(20):
+        out = oracle.shift(x, out, 0.0371, order, True)
+    assert out.min() >= q.min() - 1e-13 and out.max() <= q.max() + 1e-13
+
+
+def test_cumulative_is_conservative():
+    """Eq. 13: the in-cell cumulative at the full width is the cell mass."""
+    n = 40
+    x = wl.random_nodes(n, seed=15)
+    q = np.random.default_rng(16).random(n) + 0.5
+    cells = np.arange(n)
+    for order, lim in [(2, True), (3, True), (3, False), (4, False)]:
+        g = oracle.cell_cumulative(x, q, cells, np.diff(x), order, lim)
+        np.testing.assert_allclose(g, q * np.diff(x), rtol=1e-13, atol=0)
+        g0 = oracle.cell_cumulative(x, q, cells, np.zeros(n), order, lim)
+        assert np.all(g0 == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# equivalences stated by the paper
+# ---------------------------------------------------------------------------
+
+def test_small_shift_equals_van_leer_upwind_step():
+    """Sec. 3.2: for a shift below the smallest cell the remap is a standard upwind
+    step; with PLM the upwind flux through the swept region, evaluated at its
+    midpoint (exact for a linear profile), is the van Leer residual step with
+    dv = s / dt."""
+    n = 120
+    x = wl.random_nodes(n, seed=17)
+    q = wl.three_gaussians(x, 18)
+    s = 0.8 * np.diff(x).min()
+    dt = 0.37
+    a = oracle.shift(x, q, s, 2, True)
+    b = oracle.residual(x, q, np.full(n, s / dt), dt, oracle.VANLEER)
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-14)
+
+
+def test_uniform_mesh_shift_splits_into_roll_plus_fraction():
+    """Sec. 4.1: on a uniform mesh RAM is FARGO -- an integer roll composed with a
+    sub-cell remap."""
+    n = 128
+    x = wl.uniform_nodes(n)
+    q = wl.three_gaussians(x, 19)
+    sig = 37.41
+    a = oracle.shift(x, q, sig / n, 3, True)
+    b = np.roll(oracle.shift(x, q, (sig - 37) / n, 3, True), 37)
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-14)
+
+
+def test_worked_example_fig1():
+    """Sec. 3.4 (Fig. 1): an output cell whose shifted interval starts in cell 1,
+    covers cell 2 and ends in cell 3 gets the right part of q_1, all of M_2 and
+    the left part of q_3.  Structural check on a hand-built 6-cell mesh (the paper
+    prints no numbers for this example)."""
+    x = np.array([0.0, 0.1, 0.25, 0.33, 0.5, 0.7, 1.0])
+    q = np.array([1.0, 2.0, 4.0, 3.0, 1.5, 1.2])
+    s = 0.3  # output cell 4 = [0.5, 0.7] comes from [0.2, 0.4]: cells 1, 2, 3
+    coef = oracle.reconstruct(x, q, 2, True)
+    out = oracle.shift(x, q, s, 2, True)
+    lo, hi = x[4] - s, x[5] - s
+    assert x[1] <= lo < x[2] and x[3] <= hi < x[4]
+
+    def integ(i, a, b):
+        xc = 0.5 * (x[i] + x[i + 1])
+        return coef[i, 0] * (b - a) + 0.5 * coef[i, 1] * ((b - xc) ** 2 - (a - xc) ** 2)
+
+    m = integ(1, lo, x[2]) + q[2] * (x[3] - x[2]) + integ(3, x[3], hi)
+    assert out[4] == pytest.approx(m / (x[5] - x[4]), rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# residual step
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", [oracle.DONOR, oracle.VANLEER])
+def test_residual_zero_velocity_identity(scheme):
+    x = wl.random_nodes(64, seed=23)
+    q = np.random.default_rng(24).random(64)
+    out = oracle.residual(x, q, np.zeros(64), 0.1, scheme)
+    assert np.array_equal(out, q)
+
+
+@pytest.mark.parametrize("scheme", [oracle.DONOR, oracle.VANLEER])
+def test_residual_cfl_one_is_a_roll(scheme):
+    """Sec. 4.1 footnote: moving exactly one cell per step is exact on a uniform mesh."""
+    n = 64
+    x = wl.uniform_nodes(n)
+    q = np.random.default_rng(25).random(n)
+    dt = 0.5
+    out = oracle.residual(x, q, np.full(n, (1.0 / n) / dt), dt, scheme)
+    np.testing.assert_allclose(out, np.roll(q, 1), rtol=0, atol=1e-14)
+    out = oracle.residual(x, q, np.full(n, -(1.0 / n) / dt), dt, scheme)
+    np.testing.assert_allclose(out, np.roll(q, -1), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("scheme", [oracle.DONOR, oracle.VANLEER])
+def test_residual_conserves_and_bounds(scheme):
+    n = 200
+    x = wl.random_nodes(n, seed=26)
+    q = wl.tophat_averages(x, 0.2, 0.4) + 0.5
+    dv = 0.3 * np.sin(2 * np.pi * x[:-1]) * np.diff(x).min() / 0.1
+    out = q
+    for _ in range(10):
+        out = oracle.residual(x, out, dv, 0.1, scheme, nsub=2)
+    m0 = oracle.mass(x, q)
+    assert abs(oracle.mass(x, out) - m0) <= 1e-14 * m0
+    # with a constant velocity (no compression) donor cell adds no extrema
+    dvc = np.full(n, 0.7 * np.diff(x).min() / 0.1)
+    out = q
+    for _ in range(10):
+        out = oracle.residual(x, out, dvc, 0.1, scheme)
+    if scheme == oracle.DONOR:
+        assert out.min() >= q.min() - 1e-14 and out.max() <= q.max() + 1e-14
+
+
+def test_residual_cfl_flag():
+    n = 32
+    x = wl.uniform_nodes(n)
+    q = np.ones(n)
+    _, st = oracle.residual(x, q, np.full(n, 2.0), 1.0 / n, oracle.DONOR,
+                            return_status=True)
+    assert st == 3
+    _, st = oracle.residual(x, q, np.full(n, 2.0), 1.0 / n, oracle.DONOR, nsub=2,
+                            return_status=True)
+    assert st == 0
+
+
+def test_subcycles_equal_repeated_steps():
+    n = 50
+    x = wl.random_nodes(n, seed=27)
+    q = wl.three_gaussians(x, 28)
+    dv = 0.02 * np.cos(2 * np.pi * x[:-1])
+    a = oracle.residual(x, q, dv, 0.3, oracle.VANLEER, nsub=3)
+    b = q
+    for _ in range(3):
+        b = oracle.residual(x, b, dv, 0.1, oracle.VANLEER)
+    np.testing.assert_allclose(a, b, rtol=1e-14, atol=0)
+
+
+def test_phase_update():
+    L = 2 * np.pi
+    ph = 0.0
+    for _ in range(1000):
+        ph = oracle.phase_update(ph, 3.3, 0.7, L)
+        assert 0.0 <= ph < L
+    assert ph == pytest.approx(math.fmod(1000 * 3.3 * 0.7, L), abs=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# transpose of the linear step
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+@pytest.mark.parametrize("s", [0.013, 0.41, -1.73])
+def test_shift_adjoint_dot_product(order, s):
+    n = 90
+    x = wl.random_nodes(n, seed=51)
+    rng = np.random.default_rng(52)
+    u, v = rng.standard_normal(n), rng.standard_normal(n)
+    Au = oracle.shift(x, u, s, order, False)
+    ATv = oracle.shift_adjoint(x, v, s, order)
+    lhs, rhs = float(Au @ v), float(u @ ATv)
+    assert abs(lhs - rhs) <= 1e-13 * (np.abs(Au) @ np.abs(v))
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_shift_adjoint_dense_transpose(order):
+    n = 24
+    x = wl.random_nodes(n, seed=53)
+    s = 0.377
+    A = np.stack([oracle.shift(x, e, s, order, False) for e in np.eye(n)], axis=1)
+    AT = np.stack([oracle.shift_adjoint(x, e, s, order) for e in np.eye(n)], axis=1)
+    np.testing.assert_allclose(AT, A.T, rtol=0, atol=1e-13)
+
+
+def test_step_adjoint_dense_transpose_with_donor_residual():
+    n = 20
+    x = wl.random_nodes(n, seed=54)
+    rng = np.random.default_rng(55)
+    dv = rng.uniform(-1, 1, n) * np.diff(x).min()
+    dt, s = 0.6, 0.31
+    A = np.stack([oracle.step(x, e, s, 3, False, dv, dt, oracle.DONOR, 2)
+                  for e in np.eye(n)], axis=1)
+    AT = np.stack([oracle.step_adjoint(x, np.zeros(n), e, s, 3, dv, dt, 2)[0]
+                   for e in np.eye(n)], axis=1)
+    np.testing.assert_allclose(AT, A.T, rtol=0, atol=1e-13)
+
+
+def test_step_adjoint_dv_gradient_vs_finite_differences():
+    """d loss / d dv of the donor step against central differences; dv is kept
+    away from zero so that no upwind side flips under the perturbation."""
+    n = 40
+    x = wl.random_nodes(n, seed=56)
+    rng = np.random.default_rng(57)
+    q = wl.three_gaussians(x, 58)
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    dv = sign * (0.3 + 0.5 * rng.random(n)) * np.diff(x).min()
+    dt, s, nsub = 0.5, 0.123, 2
+    g = rng.standard_normal(n)
+    _, gdv = oracle.step_adjoint(x, q, g, s, 2, dv, dt, nsub)
+
+    def loss(d):
+        return float(g @ oracle.step(x, q, s, 2, False, d, dt, oracle.DONOR, nsub))
+
+    h = 1e-6 * np.diff(x).min()
+    for k in range(8):
+        e = rng.standard_normal(n)
+        fd = (loss(dv + h * e) - loss(dv - h * e)) / (2 * h)
+        assert fd == pytest.approx(float(gdv @ e), rel=1e-6, abs=1e-9)
