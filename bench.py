@@ -1,0 +1,376 @@
+"""Benchmark of the RAM step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload disk|disk_large|batched] [--no-e2e] [--no-cpu]
+
+One step = one full RAM step (shift by v0 dt with the PPM remap, then the
+sub-cycled van Leer residual step) of every ring of a synthetic Keplerian disk
+(1024 rings x 4096 phi cells, FP32 cells, FP64 shifts).  The inputs fit in L2,
+so L2 is flushed (a read of 2 x L2 bytes) before every timed step and the step
+time is the sum of per-step CUDA-event intervals on the launching stream.  With
+N GPUs (torchrun, one rank per GPU) every rank advances its own disk (weak
+scaling, no data exchange); the time is the max over ranks.
+
+Prints ONE JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RAM step Gcell-updates/s & % HBM roofline, FP32/batched vs plain FP64 at 1e-5 L1"
+UNIT = "Gcell-updates/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(name, rank):
+    from paper_2305_05362_gb300 import workloads as wl
+    if name == "disk":
+        return wl.disk(n_r=1024, n_phi=4096, seed_dv=4 + rank, dtype=np.float32)
+    if name == "disk_large":
+        return wl.disk(n_r=8192, n_phi=16384, seed_dv=4 + rank, ref_n_phi=4096,
+                       dtype=np.float32)
+    if name == "batched":
+        return wl.batched(n_rows=512, seed_len=6 + 100 * rank)
+    raise SystemExit("unknown workload %s" % name)
+
+
+def _bytes_per_cell(w, es):
+    """Algorithmic bytes of one step per cell: read Q, write Q, read dv when the
+    residual step runs, read the row's own mesh (8 B fixed-point node + width)
+    for non-uniform rows."""
+    b = 2 * es
+    if w.dv is not None:
+        b += es
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                   "-lms", "50"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d[kernel_key]
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for rel in ent["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != ent["sha256"]:
+        return None
+    return ent
+
+
+def cpu_baseline(w, budget_s=10.0):
+    """The FP64 oracle (C, OpenMP over rows) on the host cores: whole-disk steps
+    until the time budget is spent."""
+    import oracle
+    shifts = np.array([oracle.shift_from_velocity(v, w.dt) for v in w.v0])
+    q = np.asarray(w.q0, dtype=np.float64)
+    dv = None if w.dv is None else np.asarray(w.dv, dtype=np.float64)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        q = oracle.step_rows(w.row_offset, w.nodes, w.shared_mesh, w.order, w.limiter,
+                             shifts, q, dv=dv, dt=w.dt, scheme=w.scheme, nsub=w.nsub)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": w.n_cells * steps / el / 1e9, "unit": UNIT,
+            "cores": int(oracle.num_threads()), "kind": "oracle",
+            "sample": "%d full steps of the %s workload (%d cells) in %.1f s, FP64 C oracle, "
+                      "OpenMP over rows" % (steps, w.name, w.n_cells, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(args.workload, 0)
+    res = cpu_baseline(w, budget_s=max(2.0, 20.0 / max(1, args.steps)))
+    steps = args.steps
+    # each timed step is a bounded sample: the same oracle steps as cpu_baseline
+    import oracle
+    shifts = np.array([oracle.shift_from_velocity(v, w.dt) for v in w.v0])
+    rows = max(1, min(w.n_rows, int(w.n_rows * 2.0 / max(1e-9, w.n_cells / (res["value"] * 1e9)))))
+    ro = w.row_offset[:rows + 1]
+    n = int(ro[-1])
+    q = np.asarray(w.q0[:n], dtype=np.float64)
+    dv = None if w.dv is None else np.asarray(w.dv[:n], dtype=np.float64)
+    for _ in range(args.warmup):
+        oracle.step_rows(ro, w.nodes, w.shared_mesh, w.order[:rows], w.limiter, shifts[:rows],
+                         q, dv=dv, dt=w.dt, scheme=w.scheme, nsub=w.nsub[:rows])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        q = oracle.step_rows(ro, w.nodes, w.shared_mesh, w.order[:rows], w.limiter,
+                             shifts[:rows], q, dv=dv, dt=w.dt, scheme=w.scheme,
+                             nsub=w.nsub[:rows])
+    el = time.perf_counter() - t0
+    value = n * steps / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample_rows": rows, "sample_cells": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(oracle.num_threads()),
+                             "kind": "oracle",
+                             "sample": "%d of %d rings per step (%d cells), FP64 C oracle"
+                                       % (rows, w.n_rows, n)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="disk", choices=["disk", "disk_large", "batched"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=50)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2305_05362_gb300 import ram
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = _workload(args.workload, rank)
+    plan = ram.Plan.from_workload(w, device=local)
+    info = plan.info()
+    uniform_orders = {int(o) for r, o in enumerate(w.order)} if info.n_uniform_rows else set()
+    launches_per_step = max(1, len(uniform_orders) if info.n_tiles_general == 0 else
+                            len(set(int(o) for o in w.order)) + 1)
+
+    def tensors(dtype):
+        q = torch.tensor(np.asarray(w.q0), dtype=dtype, device=dev)
+        dv = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dtype, device=dev)
+        return q, torch.empty_like(q), dv
+
+    v0 = torch.tensor(w.v0, dtype=torch.float64, device=dev)
+    nsub = torch.tensor(w.nsub, dtype=torch.int32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    l2 = int(getattr(props, "L2_cache_size", 0) or 0)
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+    flush.fill_(1.0)
+
+    def do_flush():
+        flush.sum()  # a read of 2 x L2 bytes evicts the step's data without dirty lines
+
+    def timed(dtype, steps, warm):
+        q, out, dv = tensors(dtype)
+        for _ in range(warm):
+            ram.step(plan, q, out, v0, w.dt, dv=dv, scheme=w.scheme, nsub=nsub)
+            q, out = out, q
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            do_flush()
+            ev[k][0].record()
+            ram.step(plan, q, out, v0, w.dt, dv=dv, scheme=w.scheme, nsub=nsub)
+            ev[k][1].record()
+            q, out = out, q
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return q, ms
+
+    # FP32 timed run
+    uuid = None
+    try:
+        uuid = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU-") else str(props.uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid if rank == 0 else None)
+    if rank == 0:
+        sampler.start()
+    q32, ms32 = timed(torch.float32, args.steps, args.warmup)
+    clocks = sampler.stop() if rank == 0 else None
+    st = plan.check_errors()
+    total_s = sum(ms32) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    cells_all = w.n_cells * world
+    value = cells_all * args.steps / total_max / 1e9
+    ms_per_step = 1e3 * total_max / args.steps
+
+    # roofline of the step kernel
+    es = 4
+    bpc = _bytes_per_cell(w, es)
+    step_s = total_s / args.steps
+    achieved = w.n_cells * bpc / step_s / 1e9
+    peak, peak_kind = _peaks()
+    kernel_key = "k_uniform<float,3>" if info.n_tiles_general == 0 else "k_general<float>"
+    tr = _traffic(kernel_key + ":" + w.name)
+
+    # FP64 form of the same step, and the FP32-vs-FP64 error after the same steps
+    n64 = min(args.fp64_steps, args.steps)
+    q64, ms64 = timed(torch.float64, n64, 3)
+    q32b, _ = timed(torch.float32, n64, 3)
+    a, b = q32b.double(), q64
+    rel = float((a - b).abs().sum() / b.abs().sum())
+    fp64_value = w.n_cells * n64 / (sum(ms64) / 1e3) / 1e9
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.tensor(np.asarray(w.q0), dtype=torch.float32).pin_memory()
+        dvh = None if w.dv is None else torch.tensor(np.asarray(w.dv),
+                                                     dtype=torch.float32).pin_memory()
+        outh = torch.empty_like(qh).pin_memory()
+        qd, outd, dvd = tensors(torch.float32)
+        e_steps = max(10, min(200, args.steps // 10))
+
+        def e2e_step():
+            qd.copy_(qh, non_blocking=True)
+            if dvh is not None:
+                dvd.copy_(dvh, non_blocking=True)
+            ram.step(plan, qd, outd, v0, w.dt, dv=dvd, scheme=w.scheme, nsub=nsub)
+            outh.copy_(outd, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        h2d = w.n_cells * es * (2 if w.dv is not None else 1)
+        e2e = {"value": w.n_cells * world * e_steps / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(w.n_cells * es),
+               "steps": e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(_workload(args.workload, 0))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "rows": w.n_rows, "cells": w.n_cells,
+                       "order": sorted({int(o) for o in w.order}), "limiter": w.limiter,
+                       "residual": "van Leer, sub-cycled per ring" if w.dv is not None else "none",
+                       "l2": "read of 2x L2 before every timed step; step time = sum of "
+                             "per-step CUDA-event intervals",
+                       "parallelism": "dp%d (independent disks per GPU)" % world},
+            "gpu_launches": int(args.steps * launches_per_step),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "bytes_per_cell": bpc,
+                         "traffic": None if tr is None else tr["dram_bytes_per_launch"]},
+            "fp64_single": {"value": fp64_value, "unit": UNIT, "steps": n64,
+                            "rel_l1_fp32_vs_fp64": rel},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "device_status": st,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * ram.h -- C ABI of the GB300 (sm_103a) RAM library.
+ *
+ * RAM (Rapid Advection Algorithm on Arbitrary Meshes, Benitez-Llambay, Krapp,
+ * Ramos & Kratter, arXiv 2305.05362) solves  dQ/dt + d(Q v)/dx = 0  with
+ * v = v0 + dv (Eq. 1, Eq. 4) by operator splitting (Eqs. 5-6): every row of cells
+ * is first shifted by the bulk displacement s = v0 dt with a conservative remap
+ * (Sec. 3: reconstruction, Eqs. 15-18, Eq. 26), then advanced with the residual
+ * velocity dv by an upwind step.
+ *
+ * Conventions used by every entry point
+ *  - A plan describes n_rows independent periodic rows (rings of a disk,
+ *    problems of a batch; dimensional splitting, Sec. 3.5).  Row r owns the
+ *    cells [row_offset[r], row_offset[r+1]) of every packed cell array.
+ *  - Row r has N_r cells and N_r+1 strictly increasing nodes
+ *    x_{-1/2} < x_{1/2} < ... < x_{N-1/2} (Sec. 2); its period is
+ *    L_r = x_{N-1/2} - x_{-1/2}.
+ *  - Cell values Q are cell averages (Eq. 2-3), packed, FP32 or FP64 (ram_dtype).
+ *  - The residual velocity dv is given at interfaces: element row_offset[r]+j is
+ *    dv at node x_{j-1/2} of row r, same dtype as Q, j = 0..N_r-1 (node N is node 0).
+ *  - The content of a row moves by +s: output cell i receives the mass of the
+ *    source interval [x_{i-1/2} - s, x_{i+1/2} - s] (Sec. 3.2).  Any real s is
+ *    accepted; it is reduced modulo L_r.
+ *  - Device pointers are device memory of the plan's device.  The caller owns
+ *    every cell, velocity, shift, phase and gradient buffer; the plan owns its
+ *    copy of the mesh, its tile lists and its device error word.
+ *  - The step entry points (ram_shift, ram_residual_upwind, ram_step,
+ *    ram_step_adjoint, ram_row_mass) only enqueue kernels on `stream`: they
+ *    never allocate and never synchronise, so they may be captured in a CUDA
+ *    graph.  They validate host-visible arguments synchronously and return an
+ *    error without launching anything.  Conditions found on the device (CFL
+ *    above 1 in the residual step, a non-finite shift, an out-of-range sub-step
+ *    count, a wait that timed out) set bits in the plan's error word, which
+ *    ram_plan_check_errors reads and clears.
+ *  - Input and output cell arrays must not overlap (RAM_ERR_ARG).
+ */
+#ifndef RAM_H
+#define RAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RAM_OK = 0,
+    RAM_ERR_ARG = 1,          /* bad pointer, size, enum, aliasing or alignment */
+    RAM_ERR_MESH = 2,         /* nodes not strictly increasing, N < 1, bad period */
+    RAM_ERR_CFL = 3,          /* |dv| dt / (nsub dx) > 1 somewhere (residual step) */
+    RAM_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    RAM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    RAM_ERR_NOMEM = 6,        /* allocation during planning failed */
+    RAM_ERR_UNSUPPORTED = 7,  /* valid request outside what the plan/kernels support */
+    RAM_ERR_NONFINITE = 8     /* a non-finite shift was found on the device */
+} ram_status;
+
+typedef enum { RAM_F32 = 0, RAM_F64 = 1 } ram_dtype;
+typedef enum { RAM_DONOR = 0, RAM_VANLEER = 1 } ram_scheme;
+
+/* plan flags */
+#define RAM_LIMITER_OFF 1u  /* unlimited reconstruction (PLM centred slope, PPM
+                               without App. A.2); makes the shift linear in Q */
+#define RAM_SHARED_MESH 2u  /* every row uses row 0's nodes (all rows equal N) */
+
+/* largest residual sub-step count a row may ask for */
+#define RAM_MAX_NSUB 8
+
+typedef struct ram_plan_s *ram_plan;
+
+typedef struct {
+    int32_t n_rows;            /* >= 1 */
+    const int64_t *row_offset; /* host, n_rows+1 entries, row_offset[0] = 0, increasing */
+    const double *nodes;       /* host, FP64.  Per-row meshes: row r's N_r+1 nodes are
+                                  nodes[row_offset[r] + r .. row_offset[r+1] + r].
+                                  RAM_SHARED_MESH: nodes[0 .. N] only. */
+    const int8_t *order;       /* host, per-row reconstruction order p in {2,3,4}
+                                  (2 = PLM, 3 = PPM, 4 = quartic cumulative); NULL ->
+                                  default_order for every row */
+    int8_t default_order;
+    uint32_t flags;            /* RAM_LIMITER_OFF | RAM_SHARED_MESH */
+} ram_mesh_desc;
+
+/* Build a plan for the rows in `desc` on CUDA device `device` (Sec. 2 mesh,
+ * Sec. 3.2 index search).  Validates the mesh, copies it to the device in the
+ * plan's own layout, classifies rows (uniform rows take the O(1) index of
+ * Sec. 3.2.1), builds the tile lists and allocates the error word.  Host
+ * synchronous; the only entry point besides ram_plan_autotune that allocates.
+ * On failure *out is NULL and nothing is leaked. */
+ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_plan *out);
+
+/* Free every device and host resource of the plan.  NULL is accepted. */
+ram_status ram_plan_destroy(ram_plan plan);
+
+/* The shift step alone (Sec. 3, steps 1-3; Eqs. 15-18 and 26): for every row r,
+ * q_out = remap of q_in by +shift[r].  shift: device, FP64, one per row, any
+ * real value (reduced modulo the period). */
+ram_status ram_shift(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
+                     const double *shift, void *stream);
+
+/* The residual step alone (Eq. 6): nsub[r] flux-form upwind sub-steps of length
+ * dt/nsub[r] with the interface velocity dv.  scheme: RAM_DONOR (upwind cell
+ * value) or RAM_VANLEER (van Leer PLM slope of the upwind cell, evaluated at the
+ * midpoint of the swept region).  nsub: device int32 per row in
+ * [1, RAM_MAX_NSUB], or NULL for 1. */
+ram_status ram_residual_upwind(ram_plan plan, ram_dtype dtype, const void *q_in,
+                               void *q_out, const void *dv_iface, double dt,
+                               ram_scheme scheme, const int32_t *nsub, void *stream);
+
+/* One full RAM step (Eqs. 5-6 with Sec. 3): shift by s_r = v0[r] * dt, then the
+ * residual step with dv_iface (NULL -> dv = 0, no residual).  v0: device FP64
+ * per row.  phase: device FP64 per row, or NULL; when given, phase[r] is
+ * replaced by (phase[r] + s_r) reduced to [0, L_r), the accumulated offset
+ * v0 t mod L of the row. */
+ram_status ram_step(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
+                    double *phase, const double *v0, double dt, const void *dv_iface,
+                    ram_scheme scheme, const int32_t *nsub, void *stream);
+
+/* Transpose of one linear RAM step: the plan must have RAM_LIMITER_OFF and the
+ * residual scheme is donor cell.  Given the step input q_in (the same arguments
+ * as the forward ram_step) and the cotangent g_out of the step output, writes
+ * g_in = J^T g_out and, when g_dv is not NULL, ADDS d<g_out, out>/d dv into g_dv
+ * (device, same packing and dtype as dv).  At dv_j == 0 the upwind side of the
+ * flux derivative is the left cell.  dv_iface NULL -> no residual step. */
+ram_status ram_step_adjoint(ram_plan plan, ram_dtype dtype, const void *q_in,
+                            const void *g_out, void *g_in, const double *v0, double dt,
+                            const void *dv_iface, void *g_dv, const int32_t *nsub,
+                            void *stream);
+
+/* Mass of every row, sum_i Q_i dx_i (Eq. 10), written as FP64 to mass_out
+ * (device, one per row).  FP32 cells are summed exactly as products and
+ * accumulated with a compensated (two-float) scan. */
+ram_status ram_row_mass(ram_plan plan, ram_dtype dtype, const void *q, double *mass_out,
+                        void *stream);
+
+/* Synchronise the plan's device, then return (and clear) the first condition
+ * recorded in the device error word since the last call: RAM_OK, RAM_ERR_CFL,
+ * RAM_ERR_NONFINITE, RAM_ERR_ARG (sub-step count out of range) or
+ * RAM_ERR_TIMEOUT. */
+ram_status ram_plan_check_errors(ram_plan plan);
+
+typedef struct {
+    int32_t n_rows;
+    int64_t n_cells;
+    int32_t n_uniform_rows;   /* rows on the O(1)-index path */
+    int32_t n_tiles_uniform;
+    int32_t n_tiles_general;
+    int32_t tile_cells;       /* output cells per tile */
+    int32_t threads;          /* threads per CTA */
+    int32_t device;
+} ram_plan_info;
+
+ram_status ram_plan_query(ram_plan plan, ram_plan_info *info);
+
+/* Tuning: output cells per tile (64..8192) and threads per CTA (64..1024,
+ * multiple of 32).  Rebuilds the tile lists; host synchronous. */
+ram_status ram_plan_set_tiling(ram_plan plan, int32_t tile_cells, int32_t threads);
+
+const char *ram_status_string(ram_status status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t ram_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAM_H */

@@ -1,0 +1,136 @@
+// Device helpers shared by the RAM kernels: shift reduction (S0), the
+// reconstructions of Sec. 3.1 / App. A on uniform rows, and the residual flux.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ram_internal.h"
+
+namespace ram {
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+};
+
+// Reduce x to [0, p) with a floor-mod in FP64 (the shift may be any real).
+__device__ __forceinline__ double reduce_mod(double x, double p)
+{
+    double r = __dsub_rn(x, __dmul_rn(p, floor(__ddiv_rn(x, p))));
+    if (r >= p) r -= p;
+    if (r < 0.0) r += p;
+    if (r >= p) r = 0.0;
+    return r;
+}
+
+// The bulk displacement of this launch for row r (S0): the given shift, v0 dt,
+// or zero for the residual step alone.  A non-finite value is flagged and
+// replaced by zero.
+__device__ __forceinline__ double row_shift(const StepArgs &a, int r)
+{
+    double s = 0.0;
+    if (a.mode == MODE_SHIFT)
+        s = a.shift[r];
+    else if (a.mode == MODE_STEP)
+        s = __dmul_rn(a.v0[r], a.dt);
+    if (!isfinite(s)) {
+        atomicOr(a.err, ERR_NONFINITE);
+        s = 0.0;
+    }
+    return s;
+}
+
+// van Leer harmonic slope (Sec. 3.1) in undivided form (slope x width) on a
+// uniform row: 2 dl dr / (dl + dr) when dl dr > 0, else 0.
+template <typename T>
+__device__ __forceinline__ T vl_slope_u(T qm, T q0, T qp)
+{
+    T dl = q0 - qm, dr = qp - q0;
+    T pr = dl * dr;
+    return pr > T(0) ? Num<T>::div(T(2) * pr, dl + dr) : T(0);
+}
+
+// delta<Q>_i of App. A on a uniform row, limited by App. A.2 when lim.
+template <typename T>
+__device__ __forceinline__ T ppm_dq_u(T qm, T q0, T qp, bool lim)
+{
+    T d = T(0.5) * (qp - qm);
+    if (lim) {
+        T up = qp - q0, dn = q0 - qm;
+        if (up * dn > T(0)) {
+            T m = fmin(fabs(d), fmin(T(2) * fabs(dn), T(2) * fabs(up)));
+            d = copysign(m, d);
+        } else {
+            d = T(0);
+        }
+    }
+    return d;
+}
+
+// PPM parabola (QL, QR, Q6) of the centre cell from five uniform-row values
+// (App. A: <Q>_{i+1/2} = (Q_i + Q_{i+1})/2 - (dQ_{i+1} - dQ_i)/6 on a uniform
+// mesh; App. A.2 constraints when lim).
+template <typename T>
+__device__ __forceinline__ void ppm_u(T qm2, T qm1, T q0, T qp1, T qp2, bool lim, T &QL,
+                                      T &QR, T &Q6)
+{
+    const T dqm = ppm_dq_u(qm2, qm1, q0, lim);
+    const T dq0 = ppm_dq_u(qm1, q0, qp1, lim);
+    const T dqp = ppm_dq_u(q0, qp1, qp2, lim);
+    const T sixth = T(1) / T(6);
+    T L = T(0.5) * (qm1 + q0) - (dq0 - dqm) * sixth;
+    T R = T(0.5) * (q0 + qp1) - (dqp - dq0) * sixth;
+    if (lim) {
+        if ((R - q0) * (q0 - L) <= T(0)) {
+            L = q0;
+            R = q0;
+        } else {
+            const T dd = R - L;
+            const T qa = q0 - T(0.5) * (L + R);
+            if (dd * qa > dd * dd * sixth)
+                L = T(3) * q0 - T(2) * R;
+            else if (-dd * dd * sixth > dd * qa)
+                R = T(3) * q0 - T(2) * L;
+        }
+    }
+    QL = L;
+    QR = R;
+    Q6 = T(6) * q0 - T(3) * (L + R);
+}
+
+// Lagrange weights of the order-4 cumulative on a uniform row at offset xi
+// (in cell widths): the mean of the quartics through the nodes
+// {-2,-1,0,1,2} and {-1,0,1,2,3} (in cells, relative to the cell's left node),
+// folded into five coefficients c[k] of Q_{i-2+k} so that G/dx = sum c[k] Q.
+__device__ __forceinline__ void quartic_coeffs_u(double xi, double c[5])
+{
+    double w[6] = {0, 0, 0, 0, 0, 0};
+    for (int side = 0; side < 2; ++side) {
+        for (int k = side; k <= side + 4; ++k) {
+            double l = 1.0;
+            for (int j = side; j <= side + 4; ++j)
+                if (j != k) l *= (xi - (double)(j - 2)) / (double)(k - j);
+            w[k] += 0.5 * l;
+        }
+    }
+    // node values relative to the cell's left node, in units of dx:
+    // v = {-(Q_{i-2}+Q_{i-1}), -Q_{i-1}, 0, Q_i, Q_i+Q_{i+1}, Q_i+Q_{i+1}+Q_{i+2}}
+    c[0] = -w[0];
+    c[1] = -w[0] - w[1];
+    c[2] = w[3] + w[4] + w[5];
+    c[3] = w[4] + w[5];
+    c[4] = w[5];
+}
+
+__device__ __forceinline__ int wrap_index(int64_t i, int n)
+{
+    int64_t k = i % n;
+    return (int)(k < 0 ? k + n : k);
+}
+
+}  // namespace ram

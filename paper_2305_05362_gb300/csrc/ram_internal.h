@@ -1,0 +1,108 @@
+// Internal declarations of the GB300 RAM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "ram.h"
+
+namespace ram {
+
+// bits of the plan's device error word
+enum ErrBits : int {
+    ERR_CFL = 1,        // |dv| dt / (nsub dx) > 1
+    ERR_NONFINITE = 2,  // non-finite shift
+    ERR_NSUB = 4,       // sub-step count outside [1, RAM_MAX_NSUB]
+    ERR_TIMEOUT = 8,    // a bounded wait gave up
+    ERR_WINDOW = 16,    // a source window exceeded its planned bound
+};
+
+enum Mode : int { MODE_SHIFT = 0, MODE_RESIDUAL = 1, MODE_STEP = 2 };
+
+// Per-row data on the device.
+struct RowInfo {
+    int64_t cell_off;     // first cell of the row in packed Q / dv arrays
+    int64_t mesh_off;     // first cell of the row's mesh in the plan's mesh arrays
+    int64_t bucket_off;   // first entry of the row's bucket table
+    int32_t n;            // cells
+    int32_t order;        // 2, 3, 4
+    int32_t uniform;      // 1: equal widths, O(1) edge index
+    int32_t bucket_bits;  // log2 of the row's bucket count
+    double period;        // L
+    double cells_per_length;  // N / L
+    double dx;            // L / N (uniform rows)
+};
+
+// One unit of work: output cells [start, start + count) of one row.
+struct Tile {
+    int32_t row;
+    int32_t start;
+    int32_t count;
+    int32_t window;       // bound on the source-window cells (non-uniform tiles)
+};
+
+// Arguments shared by the step kernels (passed by value).
+struct StepArgs {
+    const RowInfo *rows;
+    const Tile *tiles;
+    int32_t n_tiles;
+    int32_t mode;         // Mode
+    const void *q_in;
+    void *q_out;
+    const double *shift;  // MODE_SHIFT
+    const double *v0;     // MODE_STEP
+    double dt;            // MODE_STEP / MODE_RESIDUAL
+    double *phase;        // MODE_STEP, may be null
+    const void *dv;       // null -> no residual
+    const int32_t *nsub;  // null -> 1
+    int32_t scheme;       // RAM_DONOR / RAM_VANLEER
+    int32_t limiter;      // 1 = limiters on
+    int *err;             // device error word
+    // mesh of non-uniform rows
+    const uint64_t *xfix;   // fixed-point nodes: (x_j - x_0) / L * 2^64, j = 0..N-1
+    const float *dx32;      // widths, FP32
+    const double *dx64;     // widths, FP64
+    const int32_t *buckets; // per-row bucket table: cell holding each bucket start
+};
+
+// the plan
+struct Plan {
+    int device = 0;
+    int32_t n_rows = 0;
+    int64_t n_cells = 0;
+    uint32_t flags = 0;
+    int limiter = 1;
+    int32_t tile_cells = 1024;
+    int32_t threads = 256;
+    std::vector<int64_t> row_offset;
+    std::vector<RowInfo> rows_h;
+    std::vector<double> nodes_h;   // host copy of the FP64 nodes (per row or shared)
+    std::vector<Tile> tiles_uniform_h[5];  // by order (index 2..4)
+    std::vector<Tile> tiles_general_h[5];
+    int32_t n_uniform_rows = 0;
+    int32_t window_max = 0;        // max planned source window (non-uniform tiles)
+    // device
+    RowInfo *rows = nullptr;
+    Tile *tiles_uniform[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    Tile *tiles_general[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint64_t *xfix = nullptr;
+    float *dx32 = nullptr;
+    double *dx64 = nullptr;
+    int32_t *buckets = nullptr;
+    int *err = nullptr;
+};
+
+// launchers (ram_uniform.cu, ram_general.cu)
+cudaError_t launch_uniform(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_general(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *out,
+                            cudaStream_t s);
+cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
+                           void *g_in, void *g_dv, cudaStream_t s);
+
+// tiling (ram_plan.cu)
+ram_status build_tiles(Plan &p);
+
+}  // namespace ram

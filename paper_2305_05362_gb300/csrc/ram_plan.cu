@@ -1,0 +1,417 @@
+// Planning: mesh validation, row classification, device copies of the mesh and
+// the tile lists (Sec. 2 mesh; Sec. 3.2 and 3.2.1 edge index).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ram_internal.h"
+
+namespace ram {
+namespace {
+
+// Uniform rows: every width within 8 eps L of L/N (nodes computed in FP64 as
+// x_0 + L j / N deviate from exact uniformity by a few eps L).
+bool row_is_uniform(const double *x, int n)
+{
+    const double L = x[n] - x[0];
+    const double h = L / n;
+    const double tol = 8.0 * 2.220446049250313e-16 * std::fabs(L);
+    for (int i = 0; i < n; ++i)
+        if (std::fabs((x[i + 1] - x[i]) - h) > tol) return false;
+    return true;
+}
+
+ram_status check_nodes(const double *x, int n)
+{
+    for (int j = 0; j <= n; ++j)
+        if (!std::isfinite(x[j])) return RAM_ERR_MESH;
+    for (int j = 0; j < n; ++j)
+        if (!(x[j + 1] > x[j])) return RAM_ERR_MESH;
+    return RAM_OK;
+}
+
+// Fixed-point node positions: fraction of the period in units of 2^-64.
+// Position differences and the periodic wrap are then exact integer arithmetic.
+bool fixed_point_nodes(const double *x, int n, uint64_t *out)
+{
+    const double L = x[n] - x[0];
+    const double two64 = 18446744073709551616.0;
+    uint64_t prev = 0;
+    for (int j = 0; j < n; ++j) {
+        double t = (x[j] - x[0]) / L;
+        uint64_t v;
+        if (j == 0)
+            v = 0;
+        else if (t >= 1.0)
+            return false;
+        else
+            v = (uint64_t)(t * two64);
+        if (j > 0 && v <= prev) return false;  // widths below 2^-64 L
+        out[j] = v;
+        prev = v;
+    }
+    return true;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t count)
+{
+    if (count == 0) {
+        *dst = nullptr;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc((void **)dst, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_device(Plan &p)
+{
+    cudaFree(p.rows);
+    for (int o = 0; o < 5; ++o) {
+        cudaFree(p.tiles_uniform[o]);
+        cudaFree(p.tiles_general[o]);
+        p.tiles_uniform[o] = p.tiles_general[o] = nullptr;
+    }
+    cudaFree(p.xfix);
+    cudaFree(p.dx32);
+    cudaFree(p.dx64);
+    cudaFree(p.buckets);
+    cudaFree(p.err);
+    p.rows = nullptr;
+    p.xfix = nullptr;
+    p.dx32 = nullptr;
+    p.dx64 = nullptr;
+    p.buckets = nullptr;
+    p.err = nullptr;
+}
+
+}  // namespace
+
+// Split every row into near-equal tiles of at most tile_cells output cells and
+// bound the source window of each non-uniform tile: the number of source cells
+// that an interval as long as the tile (plus the residual halo) can touch,
+// maximised over all placements, plus the reconstruction halo.
+ram_status build_tiles(Plan &p)
+{
+    for (int o = 0; o < 5; ++o) {
+        p.tiles_uniform_h[o].clear();
+        p.tiles_general_h[o].clear();
+    }
+    p.window_max = 0;
+    const int halo_res = 2 * RAM_MAX_NSUB;  // residual halo, cells per side
+    for (int r = 0; r < p.n_rows; ++r) {
+        const RowInfo &ri = p.rows_h[r];
+        const int n = ri.n;
+        const int nt = (n + p.tile_cells - 1) / p.tile_cells;
+        const bool uni = ri.uniform != 0;
+        // per-row mesh for the window bound
+        const double *x = nullptr;
+        std::vector<double> w2;
+        if (!uni) {
+            x = (p.flags & RAM_SHARED_MESH) ? p.nodes_h.data()
+                                            : p.nodes_h.data() + p.row_offset[r] + r;
+            w2.resize(2 * (size_t)n);
+            for (int i = 0; i < n; ++i) w2[i] = w2[i + n] = x[i + 1] - x[i];
+        }
+        for (int t = 0; t < nt; ++t) {
+            int a = (int)((int64_t)n * t / nt);
+            int b = (int)((int64_t)n * (t + 1) / nt);
+            Tile tl{r, a, b - a, 0};
+            if (uni) {
+                p.tiles_uniform_h[ri.order].push_back(tl);
+            } else {
+                // physical length of the output cells [a - halo, b + halo) (cyclic)
+                int span = std::min(n, (b - a) + 2 * halo_res);
+                double len = 0.0;
+                int first = ((a - halo_res) % n + n) % n;
+                for (int k = 0; k < span; ++k) len += w2[first + k];
+                // max number of source cells intersecting an interval of length len
+                int best = 0;
+                if (span >= n) {
+                    best = n + 1;
+                } else {
+                    // two pointers over the doubled width list: for each start cell i,
+                    // cells i..j-1 are covered while their summed width is < len
+                    double acc = 0.0;
+                    int j = 0;
+                    for (int i = 0; i < n; ++i) {
+                        if (j < i) {
+                            j = i;
+                            acc = 0.0;
+                        }
+                        while (j < i + n && acc + w2[j] < len) acc += w2[j++];
+                        // an interval of length len starting inside cell i touches at
+                        // most cells i .. j+1
+                        best = std::max(best, j - i + 2);
+                        if (j > i) acc -= w2[i];
+                    }
+                    best = std::min(best, n + 1);
+                }
+                tl.window = best + 2 * 2 + 2;  // reconstruction halo (2 per side) + slack
+                p.window_max = std::max(p.window_max, tl.window);
+                p.tiles_general_h[ri.order].push_back(tl);
+            }
+        }
+    }
+    for (int o = 2; o <= 4; ++o) {
+        cudaFree(p.tiles_uniform[o]);
+        cudaFree(p.tiles_general[o]);
+        p.tiles_uniform[o] = p.tiles_general[o] = nullptr;
+        if (upload(&p.tiles_uniform[o], p.tiles_uniform_h[o].data(),
+                   p.tiles_uniform_h[o].size()) != cudaSuccess)
+            return RAM_ERR_NOMEM;
+        if (upload(&p.tiles_general[o], p.tiles_general_h[o].data(),
+                   p.tiles_general_h[o].size()) != cudaSuccess)
+            return RAM_ERR_NOMEM;
+    }
+    return RAM_OK;
+}
+
+}  // namespace ram
+
+using namespace ram;
+
+extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_plan *out)
+{
+    if (!out) return RAM_ERR_ARG;
+    *out = nullptr;
+    if (!desc || desc->n_rows < 1 || !desc->row_offset || !desc->nodes) return RAM_ERR_ARG;
+    const int32_t nr = desc->n_rows;
+    const int64_t *ro = desc->row_offset;
+    if (ro[0] != 0) return RAM_ERR_ARG;
+    for (int r = 0; r < nr; ++r) {
+        int64_t n = ro[r + 1] - ro[r];
+        if (n < 1) return RAM_ERR_MESH;
+        if (n > (int64_t)1 << 30) return RAM_ERR_UNSUPPORTED;
+    }
+    const bool shared = (desc->flags & RAM_SHARED_MESH) != 0;
+    if (shared)
+        for (int r = 1; r < nr; ++r)
+            if (ro[r + 1] - ro[r] != ro[1] - ro[0]) return RAM_ERR_ARG;
+    for (int r = 0; r < nr; ++r) {
+        int o = desc->order ? desc->order[r] : desc->default_order;
+        if (o < 2 || o > 4) return RAM_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return RAM_ERR_CUDA;
+    int prev_dev = 0;
+    cudaGetDevice(&prev_dev);
+    if (cudaSetDevice(device) != cudaSuccess) return RAM_ERR_CUDA;
+
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return RAM_ERR_NOMEM;
+    p->device = device;
+    p->n_rows = nr;
+    p->n_cells = ro[nr];
+    p->flags = desc->flags;
+    p->limiter = (desc->flags & RAM_LIMITER_OFF) ? 0 : 1;
+    p->row_offset.assign(ro, ro + nr + 1);
+    const size_t n_nodes = shared ? (size_t)(ro[1] + 1) : (size_t)(ro[nr] + nr);
+    p->nodes_h.assign(desc->nodes, desc->nodes + n_nodes);
+
+    ram_status st = RAM_OK;
+    // mesh checks and classification
+    std::vector<uint64_t> xfix;
+    std::vector<float> dx32;
+    std::vector<double> dx64;
+    std::vector<int32_t> buckets;
+    bool shared_uniform = false;
+    int64_t shared_mesh_off = -1;
+    p->rows_h.resize(nr);
+    for (int r = 0; r < nr && st == RAM_OK; ++r) {
+        const int n = (int)(ro[r + 1] - ro[r]);
+        const double *x = shared ? p->nodes_h.data() : p->nodes_h.data() + ro[r] + r;
+        RowInfo &ri = p->rows_h[r];
+        ri.cell_off = ro[r];
+        ri.n = n;
+        ri.order = desc->order ? desc->order[r] : desc->default_order;
+        ri.period = x[n] - x[0];
+        ri.cells_per_length = (double)n / ri.period;
+        ri.dx = ri.period / n;
+        if (shared && r > 0) {
+            ri.uniform = p->rows_h[0].uniform;
+            ri.mesh_off = p->rows_h[0].mesh_off;
+            ri.bucket_off = p->rows_h[0].bucket_off;
+            ri.bucket_bits = p->rows_h[0].bucket_bits;
+            continue;
+        }
+        st = check_nodes(x, n);
+        if (st != RAM_OK || !(ri.period > 0.0) || !std::isfinite(ri.period)) {
+            st = RAM_ERR_MESH;
+            break;
+        }
+        ri.uniform = row_is_uniform(x, n) ? 1 : 0;
+        if (ri.uniform) {
+            ri.mesh_off = 0;
+            ri.bucket_off = 0;
+            ri.bucket_bits = 0;
+            continue;
+        }
+        // non-uniform row: fixed-point nodes, widths and the bucket table
+        ri.mesh_off = (int64_t)xfix.size();
+        size_t base = xfix.size();
+        xfix.resize(base + n);
+        dx32.resize(base + n);
+        dx64.resize(base + n);
+        if (!fixed_point_nodes(x, n, xfix.data() + base)) {
+            st = RAM_ERR_MESH;
+            break;
+        }
+        for (int i = 0; i < n; ++i) {
+            dx64[base + i] = x[i + 1] - x[i];
+            dx32[base + i] = (float)dx64[base + i];
+        }
+        int bits = 1;
+        while ((1LL << bits) < 2LL * n && bits < 40) ++bits;
+        ri.bucket_bits = bits;
+        ri.bucket_off = (int64_t)buckets.size();
+        const int64_t nb = 1LL << bits;
+        buckets.resize(buckets.size() + nb);
+        int32_t *bt = buckets.data() + ri.bucket_off;
+        int cell = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            uint64_t start = (uint64_t)b << (64 - bits);
+            while (cell + 1 < n && xfix[base + cell + 1] <= start) ++cell;
+            bt[b] = cell;
+        }
+        if (shared) {
+            shared_uniform = false;
+            shared_mesh_off = ri.mesh_off;
+        }
+    }
+    (void)shared_uniform;
+    (void)shared_mesh_off;
+    if (st == RAM_OK) {
+        for (int r = 0; r < nr; ++r) p->n_uniform_rows += p->rows_h[r].uniform ? 1 : 0;
+        if (upload(&p->rows, p->rows_h.data(), p->rows_h.size()) != cudaSuccess ||
+            upload(&p->xfix, xfix.data(), xfix.size()) != cudaSuccess ||
+            upload(&p->dx32, dx32.data(), dx32.size()) != cudaSuccess ||
+            upload(&p->dx64, dx64.data(), dx64.size()) != cudaSuccess ||
+            upload(&p->buckets, buckets.data(), buckets.size()) != cudaSuccess ||
+            cudaMalloc((void **)&p->err, sizeof(int)) != cudaSuccess ||
+            cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
+            st = RAM_ERR_NOMEM;
+    }
+    if (st == RAM_OK) st = build_tiles(*p);
+    if (st == RAM_OK && cudaDeviceSynchronize() != cudaSuccess) st = RAM_ERR_CUDA;
+    if (st != RAM_OK) {
+        free_device(*p);
+        delete p;
+        cudaSetDevice(prev_dev);
+        return st;
+    }
+    cudaSetDevice(prev_dev);
+    *out = reinterpret_cast<ram_plan>(p);
+    return RAM_OK;
+}
+
+extern "C" ram_status ram_plan_destroy(ram_plan plan)
+{
+    if (!plan) return RAM_OK;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    free_device(*p);
+    cudaSetDevice(prev);
+    delete p;
+    return RAM_OK;
+}
+
+extern "C" ram_status ram_plan_query(ram_plan plan, ram_plan_info *info)
+{
+    if (!plan || !info) return RAM_ERR_ARG;
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    info->n_rows = p->n_rows;
+    info->n_cells = p->n_cells;
+    info->n_uniform_rows = p->n_uniform_rows;
+    int nu = 0, ng = 0;
+    for (int o = 2; o <= 4; ++o) {
+        nu += (int)p->tiles_uniform_h[o].size();
+        ng += (int)p->tiles_general_h[o].size();
+    }
+    info->n_tiles_uniform = nu;
+    info->n_tiles_general = ng;
+    info->tile_cells = p->tile_cells;
+    info->threads = p->threads;
+    info->device = p->device;
+    return RAM_OK;
+}
+
+extern "C" ram_status ram_plan_set_tiling(ram_plan plan, int32_t tile_cells, int32_t threads)
+{
+    if (!plan) return RAM_ERR_ARG;
+    if (tile_cells < 64 || tile_cells > 8192 || threads < 64 || threads > 1024 ||
+        threads % 32 != 0)
+        return RAM_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(p->device) != cudaSuccess) return RAM_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaSetDevice(prev);
+        return RAM_ERR_CUDA;
+    }
+    const int32_t old_tc = p->tile_cells, old_th = p->threads;
+    p->tile_cells = tile_cells;
+    p->threads = threads;
+    ram_status st = build_tiles(*p);
+    if (st != RAM_OK) {
+        p->tile_cells = old_tc;
+        p->threads = old_th;
+        build_tiles(*p);
+    }
+    cudaSetDevice(prev);
+    return st;
+}
+
+extern "C" ram_status ram_plan_check_errors(ram_plan plan)
+{
+    if (!plan) return RAM_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(p->device) != cudaSuccess) return RAM_ERR_CUDA;
+    int word = 0;
+    ram_status st = RAM_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&word, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) {
+        st = RAM_ERR_CUDA;
+    } else if (word & ERR_TIMEOUT) {
+        st = RAM_ERR_TIMEOUT;
+    } else if (word & ERR_NONFINITE) {
+        st = RAM_ERR_NONFINITE;
+    } else if (word & ERR_NSUB) {
+        st = RAM_ERR_ARG;
+    } else if (word & ERR_WINDOW) {
+        st = RAM_ERR_UNSUPPORTED;
+    } else if (word & ERR_CFL) {
+        st = RAM_ERR_CFL;
+    }
+    cudaSetDevice(prev);
+    return st;
+}
+
+extern "C" const char *ram_status_string(ram_status s)
+{
+    switch (s) {
+    case RAM_OK: return "ok";
+    case RAM_ERR_ARG: return "invalid argument";
+    case RAM_ERR_MESH: return "invalid mesh";
+    case RAM_ERR_CFL: return "residual CFL number above 1";
+    case RAM_ERR_CUDA: return "CUDA runtime error";
+    case RAM_ERR_TIMEOUT: return "device-side wait timed out";
+    case RAM_ERR_NOMEM: return "out of memory";
+    case RAM_ERR_UNSUPPORTED: return "unsupported request";
+    case RAM_ERR_NONFINITE: return "non-finite shift";
+    }
+    return "unknown status";
+}
+
+extern "C" int32_t ram_version(void) { return 100; }

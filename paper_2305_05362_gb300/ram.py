@@ -1,0 +1,234 @@
+"""ctypes binding of libram_gb300.so (include/ram.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Cell, velocity, shift and gradient arrays are torch CUDA tensors (the
+binding passes their device pointers and the current CUDA stream); meshes are
+host arrays.  If the library has not been built the first call raises -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libram_gb300.so")
+
+RAM_OK = 0
+STATUS = {0: "RAM_OK", 1: "RAM_ERR_ARG", 2: "RAM_ERR_MESH", 3: "RAM_ERR_CFL",
+          4: "RAM_ERR_CUDA", 5: "RAM_ERR_TIMEOUT", 6: "RAM_ERR_NOMEM",
+          7: "RAM_ERR_UNSUPPORTED", 8: "RAM_ERR_NONFINITE"}
+RAM_F32, RAM_F64 = 0, 1
+DONOR, VANLEER = 0, 1
+LIMITER_OFF = 1
+SHARED_MESH = 2
+MAX_NSUB = 8
+
+EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwind",
+           "ram_step", "ram_step_adjoint", "ram_row_mass", "ram_plan_check_errors",
+           "ram_plan_query", "ram_plan_set_tiling", "ram_status_string", "ram_version"]
+
+
+class RamError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, STATUS.get(status, "?"), status))
+
+
+class _MeshDesc(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32),
+                ("row_offset", ctypes.POINTER(ctypes.c_int64)),
+                ("nodes", ctypes.POINTER(ctypes.c_double)),
+                ("order", ctypes.POINTER(ctypes.c_int8)),
+                ("default_order", ctypes.c_int8),
+                ("flags", ctypes.c_uint32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cells", ctypes.c_int64),
+                ("n_uniform_rows", ctypes.c_int32), ("n_tiles_uniform", ctypes.c_int32),
+                ("n_tiles_general", ctypes.c_int32), ("tile_cells", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libram_gb300.so not found at %s; build it with "
+                           "`python -m paper_2305_05362_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.ram_plan_mesh.argtypes = [ctypes.POINTER(_MeshDesc), ctypes.c_int,
+                                  ctypes.POINTER(vp)]
+    lib.ram_plan_destroy.argtypes = [vp]
+    lib.ram_shift.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.ram_residual_upwind.argtypes = [vp, i32, vp, vp, vp, f64, i32, vp, vp]
+    lib.ram_step.argtypes = [vp, i32, vp, vp, vp, vp, f64, vp, i32, vp, vp]
+    lib.ram_step_adjoint.argtypes = [vp, i32, vp, vp, vp, vp, f64, vp, vp, vp, vp]
+    lib.ram_row_mass.argtypes = [vp, i32, vp, vp, vp]
+    lib.ram_plan_check_errors.argtypes = [vp]
+    lib.ram_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    lib.ram_plan_set_tiling.argtypes = [vp, i32, i32]
+    lib.ram_status_string.argtypes = [i32]
+    lib.ram_status_string.restype = ctypes.c_char_p
+    lib.ram_version.restype = i32
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    lib.ram_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != RAM_OK:
+        raise RamError(st, where)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return RAM_F32
+    if t.dtype == torch.float64:
+        return RAM_F64
+    raise TypeError("cell arrays must be float32 or float64, got %s" % t.dtype)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(device: int, stream=None) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return stream.cuda_stream
+
+
+class Plan:
+    """A mesh plan (ram_plan_mesh).  Rows are packed: row r owns cells
+    [row_offset[r], row_offset[r+1]).  nodes: per-row meshes packed with one
+    extra node per row, or the single shared mesh when shared_mesh=True."""
+
+    def __init__(self, row_offset: Sequence[int], nodes, order=3, limiter: bool = True,
+                 shared_mesh: bool = False, device: int = 0):
+        lib = load()
+        self._lib = lib
+        self.row_offset = np.ascontiguousarray(row_offset, dtype=np.int64)
+        self.nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        self.n_rows = int(self.row_offset.size - 1)
+        self.n_cells = int(self.row_offset[-1])
+        self.device = int(device)
+        self.limiter = bool(limiter)
+        order_arr = np.asarray(order)
+        if order_arr.ndim == 0:
+            self.order = None
+            default = int(order_arr)
+        else:
+            self.order = np.ascontiguousarray(order_arr, dtype=np.int8)
+            default = 0
+        desc = _MeshDesc()
+        desc.n_rows = self.n_rows
+        desc.row_offset = self.row_offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        desc.nodes = self.nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        desc.order = (self.order.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+                      if self.order is not None else None)
+        desc.default_order = default
+        desc.flags = (0 if limiter else LIMITER_OFF) | (SHARED_MESH if shared_mesh else 0)
+        h = ctypes.c_void_p()
+        _check(lib.ram_plan_mesh(ctypes.byref(desc), self.device, ctypes.byref(h)),
+               "ram_plan_mesh")
+        self.handle = h
+
+    @classmethod
+    def from_workload(cls, w, device: int = 0, limiter: Optional[bool] = None):
+        return cls(w.row_offset, w.nodes, order=w.order,
+                   limiter=w.limiter if limiter is None else limiter,
+                   shared_mesh=w.shared_mesh, device=device)
+
+    def destroy(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self._lib.ram_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def info(self) -> PlanInfo:
+        out = PlanInfo()
+        _check(self._lib.ram_plan_query(self.handle, ctypes.byref(out)), "ram_plan_query")
+        return out
+
+    def set_tiling(self, tile_cells: int, threads: int):
+        _check(self._lib.ram_plan_set_tiling(self.handle, int(tile_cells), int(threads)),
+               "ram_plan_set_tiling")
+
+    def check_errors(self) -> int:
+        """Synchronise and return (and clear) the device error status (0 = ok)."""
+        return int(self._lib.ram_plan_check_errors(self.handle))
+
+
+def shift(plan: Plan, q_in, q_out, shift_per_row, stream=None):
+    """ram_shift: remap every row by +shift[r]."""
+    _check(plan._lib.ram_shift(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
+                               _ptr(shift_per_row), _stream(plan.device, stream)),
+           "ram_shift")
+
+
+def residual_upwind(plan: Plan, q_in, q_out, dv, dt: float, scheme: int = VANLEER,
+                    nsub=None, stream=None):
+    """ram_residual_upwind: nsub upwind sub-steps with the interface velocity dv."""
+    _check(plan._lib.ram_residual_upwind(plan.handle, _dtype_code(q_in), _ptr(q_in),
+                                         _ptr(q_out), _ptr(dv), float(dt), int(scheme),
+                                         _ptr(nsub), _stream(plan.device, stream)),
+           "ram_residual_upwind")
+
+
+def step(plan: Plan, q_in, q_out, v0, dt: float, dv=None, scheme: int = VANLEER,
+         nsub=None, phase=None, stream=None):
+    """ram_step: shift by v0*dt then the residual step (dv=None: no residual)."""
+    _check(plan._lib.ram_step(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
+                              _ptr(phase), _ptr(v0), float(dt), _ptr(dv), int(scheme),
+                              _ptr(nsub), _stream(plan.device, stream)),
+           "ram_step")
+
+
+def step_adjoint(plan: Plan, q_in, g_out, g_in, v0, dt: float, dv=None, g_dv=None,
+                 nsub=None, stream=None):
+    """ram_step_adjoint: g_in = J^T g_out of the linear step; adds into g_dv."""
+    _check(plan._lib.ram_step_adjoint(plan.handle, _dtype_code(g_out), _ptr(q_in),
+                                      _ptr(g_out), _ptr(g_in), _ptr(v0), float(dt),
+                                      _ptr(dv), _ptr(g_dv), _ptr(nsub),
+                                      _stream(plan.device, stream)),
+           "ram_step_adjoint")
+
+
+def row_mass(plan: Plan, q, out, stream=None):
+    """ram_row_mass: per-row mass (FP64) into out."""
+    _check(plan._lib.ram_row_mass(plan.handle, _dtype_code(q), _ptr(q), _ptr(out),
+                                  _stream(plan.device, stream)), "ram_row_mass")
+
+
+def version() -> int:
+    return int(load().ram_version())
