@@ -153,8 +153,36 @@ typedef struct {
 ram_status ram_plan_query(ram_plan plan, ram_plan_info *info);
 
 /* Tuning: output cells per tile (64..8192) and threads per CTA (64..1024,
- * multiple of 32).  Rebuilds the tile lists; host synchronous. */
+ * multiple of 32) of the tiled kernels.  Rebuilds the tile lists; host
+ * synchronous. */
 ram_status ram_plan_set_tiling(ram_plan plan, int32_t tile_cells, int32_t threads);
+
+/* Launch shapes of a plan's kernels. */
+typedef struct {
+    int32_t rows_cells_per_thread_f32;  /* whole-row kernel, FP32: 5, 7, 9, 11 or 15 */
+    int32_t rows_cells_per_thread_f64;  /* whole-row kernel, FP64 */
+    int32_t tile_cells;                 /* tiled kernels: output cells per tile */
+    int32_t threads;                    /* tiled kernels: threads per CTA */
+    int32_t uniform_kernel_f32;         /* uniform rows, FP32: 0 = persistent whole-row
+                                           kernel (TMA-staged rows), 1 = warp segments */
+    int32_t uniform_kernel_f64;         /* the same for FP64 */
+} ram_tuning;
+
+ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out);
+/* Host synchronous (rebuilds the tile lists when the tile shape changes). */
+ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *tuning);
+
+/* Autotuner: times every candidate launch shape of the kernels this plan uses
+ * on the caller's buffers -- the arguments of ram_step, without the phase --
+ * with CUDA events on `stream` (`reps` timed steps per candidate) and keeps the
+ * fastest in the plan.  Candidates: for uniform rows the warp-segment kernel and
+ * the persistent whole-row kernel with cells per thread {5,7,9,11,15}; tile cells
+ * {256,512,1024,2048} x threads {128,256} of the tiled kernels.  Host
+ * synchronous; overwrites q_out. */
+ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
+                             const double *v0, double dt, const void *dv_iface,
+                             ram_scheme scheme, const int32_t *nsub, int32_t reps,
+                             void *stream);
 
 const char *ram_status_string(ram_status status);
 

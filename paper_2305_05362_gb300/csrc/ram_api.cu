@@ -67,7 +67,8 @@ ram_status run(const Plan *p, ram_dtype dt, const StepArgs &a, void *stream)
     DeviceGuard g(p->device);
     if (!g.ok) return RAM_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_uniform(*p, dt, a, s);
+    cudaError_t e = launch_params(*p, dt, a, s);
+    if (e == cudaSuccess) e = launch_uniform(*p, dt, a, s);
     if (e == cudaSuccess) e = launch_general(*p, dt, a, s);
     if (e == cudaErrorNotSupported) return RAM_ERR_UNSUPPORTED;
     return e == cudaSuccess ? RAM_OK : RAM_ERR_CUDA;

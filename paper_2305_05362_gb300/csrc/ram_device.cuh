@@ -28,6 +28,25 @@ __device__ __forceinline__ double reduce_mod(double x, double p)
     return r;
 }
 
+// Floor-mod with a precomputed reciprocal of the period: no FP64 divide (an FP64
+// divide costs hundreds of cycles of latency on this part).  The result is
+// brought into [0, p) by the fix-ups below.
+__device__ __forceinline__ double reduce_mod_rcp(double x, double p, double inv_p)
+{
+    double r = fma(-p, floor(x * inv_p), x);
+    if (r >= p) r -= p;
+    if (r < 0.0) r += p;
+    if (r >= p) r = 0.0;
+    return r;
+}
+
+// 1/n for the residual sub-step counts 0..RAM_MAX_NSUB
+__device__ __forceinline__ double inv_small(int n)
+{
+    const double t[9] = {0.0, 1.0, 0.5, 1.0 / 3.0, 0.25, 0.2, 1.0 / 6.0, 1.0 / 7.0, 0.125};
+    return t[n];
+}
+
 // The bulk displacement of this launch for row r (S0): the given shift, v0 dt,
 // or zero for the residual step alone.  A non-finite value is flagged and
 // replaced by zero.
@@ -107,15 +126,20 @@ __device__ __forceinline__ void ppm_u(T qm2, T qm1, T q0, T qp1, T qp2, bool lim
 // (in cell widths): the mean of the quartics through the nodes
 // {-2,-1,0,1,2} and {-1,0,1,2,3} (in cells, relative to the cell's left node),
 // folded into five coefficients c[k] of Q_{i-2+k} so that G/dx = sum c[k] Q.
+// The Lagrange denominators of five equally spaced nodes are 24, -6, 4, -6, 24.
 __device__ __forceinline__ void quartic_coeffs_u(double xi, double c[5])
 {
+    const double inv_den[5] = {1.0 / 24.0, -1.0 / 6.0, 0.25, -1.0 / 6.0, 1.0 / 24.0};
     double w[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
-        for (int k = side; k <= side + 4; ++k) {
-            double l = 1.0;
-            for (int j = side; j <= side + 4; ++j)
-                if (j != k) l *= (xi - (double)(j - 2)) / (double)(k - j);
-            w[k] += 0.5 * l;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double l = inv_den[k];
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (j != k) l *= xi - (double)(side + j - 2);
+            w[side + k] += 0.5 * l;
         }
     }
     // node values relative to the cell's left node, in units of dx:
@@ -125,6 +149,16 @@ __device__ __forceinline__ void quartic_coeffs_u(double xi, double c[5])
     c[2] = w[3] + w[4] + w[5];
     c[3] = w[4] + w[5];
     c[4] = w[5];
+}
+
+// Wait until the kernels this one depends on (programmatic dependent launch)
+// have finished and their writes are visible; a no-op for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next kernel in the stream launch now (it waits for this one's results
+// with pdl_wait).
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ int wrap_index(int64_t i, int n)

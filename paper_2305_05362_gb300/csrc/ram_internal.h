@@ -33,6 +33,7 @@ struct RowInfo {
     double period;        // L
     double cells_per_length;  // N / L
     double dx;            // L / N (uniform rows)
+    double inv_period;    // 1 / L
 };
 
 // One unit of work: output cells [start, start + count) of one row.
@@ -67,6 +68,18 @@ struct StepArgs {
     const int32_t *buckets; // per-row bucket table: cell holding each bucket start
 };
 
+// Shift parameters of one uniform row for one launch (S0), written by the
+// parameter kernel and read by the uniform-row kernels.
+template <typename T> struct RowParams {
+    int64_t cell_off;  // first cell of the row in the packed arrays
+    int32_t n;         // cells
+    int32_t K;         // whole cells of the shift, in [0, n)
+    int32_t whole;     // the shift is a whole number of cells
+    int32_t nsub;      // residual sub-steps (0: no residual in this launch)
+    T c[5];            // partial-integral coefficients at the edge offset
+    T cf;              // Courant number per unit dv of one sub-step
+};
+
 // the plan
 struct Plan {
     int device = 0;
@@ -76,23 +89,61 @@ struct Plan {
     int limiter = 1;
     int32_t tile_cells = 1024;
     int32_t threads = 256;
+    int32_t rows_v[2] = {7, 7};    // cells per thread of the whole-row kernel (FP32, FP64)
     std::vector<int64_t> row_offset;
     std::vector<RowInfo> rows_h;
     std::vector<double> nodes_h;   // host copy of the FP64 nodes (per row or shared)
-    std::vector<Tile> tiles_uniform_h[5];  // by order (index 2..4)
+    std::vector<Tile> tiles_uniform_h[5];  // by order (index 2..4): every uniform row
     std::vector<Tile> tiles_general_h[5];
+    // uniform rows taken by the persistent whole-row kernel, per dtype and order, and
+    // the tiles of the remaining uniform rows
+    std::vector<int32_t> rows_fit_h[2][5];
+    std::vector<Tile> tiles_rest_h[2][5];
+    int32_t ncap_fit[2][5] = {{0}};
+    // uniform rows taken by the warp-segment kernel, and the tiles of the others
+    std::vector<int32_t> rows_seg_h[2][5];
+    std::vector<Tile> tiles_rest_seg_h[2][5];
+    int32_t uniform_kernel[2] = {1, 1};  // 0: persistent whole-row, 1: warp segments
     int32_t n_uniform_rows = 0;
     int32_t window_max = 0;        // max planned source window (non-uniform tiles)
     // device
     RowInfo *rows = nullptr;
     Tile *tiles_uniform[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     Tile *tiles_general[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t *rows_fit[2][5] = {{nullptr}};
+    Tile *tiles_rest[2][5] = {{nullptr}};
+    int32_t *rows_seg[2][5] = {{nullptr}};
+    Tile *tiles_rest_seg[2][5] = {{nullptr}};
+    void *row_par = nullptr;        // RowParams<double> per row (FP32 launches use the first
+                                    // half of each slot as RowParams<float>)
     uint64_t *xfix = nullptr;
     float *dx32 = nullptr;
     double *dx64 = nullptr;
     int32_t *buckets = nullptr;
     int *err = nullptr;
 };
+
+// per-row shift parameters of the uniform rows (ram_params.cu)
+cudaError_t launch_params(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s);
+// launch with programmatic stream serialization (the kernel may start before
+// the previous kernel in the stream finishes; it calls griddepcontrol.wait
+// before touching that kernel's results)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // launchers (ram_uniform.cu, ram_general.cu)
 cudaError_t launch_uniform(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s);
@@ -102,7 +153,19 @@ cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *
 cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
                            void *g_in, void *g_dv, cudaStream_t s);
 
+cudaError_t launch_rows(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
+                        int order, const int32_t *row_ids, int n_rows, int ncap);
+cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
+                        int order, const int32_t *row_ids, int n_rows);
+
 // tiling (ram_plan.cu)
 ram_status build_tiles(Plan &p);
+
+// Largest row length (cells) the persistent whole-row kernel stages in shared memory.
+int rows_kernel_max_cells(ram_dtype dt);
+
+// Cells-per-thread values the whole-row kernel is built for (autotuner candidates).
+extern const int kRowsVCandidates[];
+extern const int kRowsVCount;
 
 }  // namespace ram

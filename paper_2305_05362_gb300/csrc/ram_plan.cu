@@ -68,19 +68,36 @@ cudaError_t upload(T **dst, const T *src, size_t count)
     return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-void free_device(Plan &p)
+void free_lists(Plan &p)
 {
-    cudaFree(p.rows);
     for (int o = 0; o < 5; ++o) {
         cudaFree(p.tiles_uniform[o]);
         cudaFree(p.tiles_general[o]);
         p.tiles_uniform[o] = p.tiles_general[o] = nullptr;
+        for (int d = 0; d < 2; ++d) {
+            cudaFree(p.rows_fit[d][o]);
+            cudaFree(p.tiles_rest[d][o]);
+            cudaFree(p.rows_seg[d][o]);
+            cudaFree(p.tiles_rest_seg[d][o]);
+            p.rows_fit[d][o] = nullptr;
+            p.tiles_rest[d][o] = nullptr;
+            p.rows_seg[d][o] = nullptr;
+            p.tiles_rest_seg[d][o] = nullptr;
+        }
     }
+}
+
+void free_device(Plan &p)
+{
+    cudaFree(p.rows);
+    free_lists(p);
     cudaFree(p.xfix);
     cudaFree(p.dx32);
     cudaFree(p.dx64);
     cudaFree(p.buckets);
     cudaFree(p.err);
+    cudaFree(p.row_par);
+    p.row_par = nullptr;
     p.rows = nullptr;
     p.xfix = nullptr;
     p.dx32 = nullptr;
@@ -97,9 +114,17 @@ void free_device(Plan &p)
 // maximised over all placements, plus the reconstruction halo.
 ram_status build_tiles(Plan &p)
 {
+    free_lists(p);
     for (int o = 0; o < 5; ++o) {
         p.tiles_uniform_h[o].clear();
         p.tiles_general_h[o].clear();
+        for (int d = 0; d < 2; ++d) {
+            p.rows_fit_h[d][o].clear();
+            p.tiles_rest_h[d][o].clear();
+            p.ncap_fit[d][o] = 0;
+            p.rows_seg_h[d][o].clear();
+            p.tiles_rest_seg_h[d][o].clear();
+        }
     }
     p.window_max = 0;
     const int halo_res = 2 * RAM_MAX_NSUB;  // residual halo, cells per side
@@ -123,6 +148,30 @@ ram_status build_tiles(Plan &p)
             Tile tl{r, a, b - a, 0};
             if (uni) {
                 p.tiles_uniform_h[ri.order].push_back(tl);
+                // persistent whole-row kernel: TMA needs 16-byte aligned row starts and
+                // lengths, and the row (plus halos) must fit the shared-memory stages
+                for (int d = 0; d < 2; ++d) {
+                    const int es = d == 0 ? 4 : 8;
+                    const bool fit = n >= 32 && n <= rows_kernel_max_cells((ram_dtype)d) &&
+                                     (n * es) % 16 == 0 && (ri.cell_off * es) % 16 == 0;
+                    if (fit) {
+                        if (t == 0) {
+                            p.rows_fit_h[d][ri.order].push_back(r);
+                            int cap = (n + 15) / 16 * 16;
+                            if (cap > p.ncap_fit[d][ri.order]) p.ncap_fit[d][ri.order] = cap;
+                        }
+                    } else {
+                        p.tiles_rest_h[d][ri.order].push_back(tl);
+                    }
+                    // warp-segment kernel: 16-byte aligned rows of at least 512 cells
+                    const bool seg = n >= 512 && (n * es) % 16 == 0 &&
+                                     (ri.cell_off * es) % 16 == 0;
+                    if (seg) {
+                        if (t == 0) p.rows_seg_h[d][ri.order].push_back(r);
+                    } else {
+                        p.tiles_rest_seg_h[d][ri.order].push_back(tl);
+                    }
+                }
             } else {
                 // physical length of the output cells [a - halo, b + halo) (cyclic)
                 int span = std::min(n, (b - a) + 2 * halo_res);
@@ -158,15 +207,26 @@ ram_status build_tiles(Plan &p)
         }
     }
     for (int o = 2; o <= 4; ++o) {
-        cudaFree(p.tiles_uniform[o]);
-        cudaFree(p.tiles_general[o]);
-        p.tiles_uniform[o] = p.tiles_general[o] = nullptr;
         if (upload(&p.tiles_uniform[o], p.tiles_uniform_h[o].data(),
                    p.tiles_uniform_h[o].size()) != cudaSuccess)
             return RAM_ERR_NOMEM;
         if (upload(&p.tiles_general[o], p.tiles_general_h[o].data(),
                    p.tiles_general_h[o].size()) != cudaSuccess)
             return RAM_ERR_NOMEM;
+        for (int d = 0; d < 2; ++d) {
+            if (upload(&p.rows_fit[d][o], p.rows_fit_h[d][o].data(),
+                       p.rows_fit_h[d][o].size()) != cudaSuccess)
+                return RAM_ERR_NOMEM;
+            if (upload(&p.tiles_rest[d][o], p.tiles_rest_h[d][o].data(),
+                       p.tiles_rest_h[d][o].size()) != cudaSuccess)
+                return RAM_ERR_NOMEM;
+            if (upload(&p.rows_seg[d][o], p.rows_seg_h[d][o].data(),
+                       p.rows_seg_h[d][o].size()) != cudaSuccess)
+                return RAM_ERR_NOMEM;
+            if (upload(&p.tiles_rest_seg[d][o], p.tiles_rest_seg_h[d][o].data(),
+                       p.tiles_rest_seg_h[d][o].size()) != cudaSuccess)
+                return RAM_ERR_NOMEM;
+        }
     }
     return RAM_OK;
 }
@@ -233,6 +293,7 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
         ri.period = x[n] - x[0];
         ri.cells_per_length = (double)n / ri.period;
         ri.dx = ri.period / n;
+        ri.inv_period = 1.0 / ri.period;
         if (shared && r > 0) {
             ri.uniform = p->rows_h[0].uniform;
             ri.mesh_off = p->rows_h[0].mesh_off;
@@ -294,6 +355,7 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
             upload(&p->dx64, dx64.data(), dx64.size()) != cudaSuccess ||
             upload(&p->buckets, buckets.data(), buckets.size()) != cudaSuccess ||
             cudaMalloc((void **)&p->err, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&p->row_par, sizeof(RowParams<double>) * (size_t)nr) != cudaSuccess ||
             cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
             st = RAM_ERR_NOMEM;
     }

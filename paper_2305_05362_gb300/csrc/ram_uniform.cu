@@ -10,6 +10,9 @@
 // and the residual sub-steps (Eq. 6) stay on chip; the tile is written once.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+#include <vector>
+
 #include "ram_device.cuh"
 
 namespace ram {
@@ -18,7 +21,8 @@ namespace {
 constexpr int kMaxHalo = 2 * RAM_MAX_NSUB;  // residual halo (cells per side)
 
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(1024) k_uniform(StepArgs a, int tile_cap)
+__global__ void __launch_bounds__(1024)
+    k_uniform(StepArgs a, int tile_cap, const RowParams<T> *pars)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int HR = (ORDER == 2) ? 1 : 2;  // reconstruction halo
@@ -31,61 +35,23 @@ __global__ void __launch_bounds__(1024) k_uniform(StepArgs a, int tile_cap)
     T *sV = sP2 + qcap;                       // dv at interfaces
     T *sF = sV + qcap;                        // fluxes
 
-    __shared__ long long s_K;
-    __shared__ double s_f;
-    __shared__ T s_c[5];
-
     const Tile tile = a.tiles[blockIdx.x];
     const RowInfo row = a.rows[tile.row];
     const int N = row.n;
     const int tid = threadIdx.x, nth = blockDim.x;
+    // the row's shift parameters come from the parameter kernel launched just before
+    pdl_wait();
+    const RowParams<T> P = pars[tile.row];
 
-    if (tid == 0) {
-        const double s = row_shift(a, tile.row);
-        if (a.mode == MODE_STEP && a.phase != nullptr && tile.start == 0)
-            a.phase[tile.row] = reduce_mod(a.phase[tile.row] + s, row.period);
-        // reduce the shift modulo the period first (a whole number of periods is
-        // then exactly no shift), then express it in cells: K whole cells plus a
-        // fraction f in [0, 1)
-        double sig = __dmul_rn(reduce_mod(s, row.period), row.cells_per_length);
-        if (sig >= (double)N) sig -= (double)N;
-        const double Kd = floor(sig);
-        s_K = (long long)Kd;
-        s_f = sig - Kd;
-        // source offset of every shifted edge inside its cell, in widths
-        const double xi = 1.0 - s_f;
-        if (ORDER == 2) {
-            s_c[0] = (T)xi;
-            s_c[1] = (T)(0.5 * (xi * xi - xi));
-        } else if (ORDER == 3) {
-            // g(xi) = QL (xi - xi^2/2) + QR xi^2/2 + Q6 (xi^2/2 - xi^3/3)
-            s_c[0] = (T)(xi - 0.5 * xi * xi);
-            s_c[1] = (T)(0.5 * xi * xi);
-            s_c[2] = (T)(0.5 * xi * xi - xi * xi * xi / 3.0);
-        } else {
-            double c[5];
-            quartic_coeffs_u(xi, c);
-            for (int k = 0; k < 5; ++k) s_c[k] = (T)c[k];
-        }
-    }
-    __syncthreads();
-
-    const bool residual = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
-    int nsub = 0;
-    if (residual) {
-        nsub = a.nsub ? a.nsub[tile.row] : 1;
-        if (nsub < 1 || nsub > RAM_MAX_NSUB) {
-            if (tid == 0) atomicOr(a.err, ERR_NSUB);
-            nsub = nsub < 1 ? 1 : RAM_MAX_NSUB;
-        }
-    }
+    const bool residual = P.nsub > 0;
+    const int nsub = P.nsub;
     const int R = (a.scheme == RAM_VANLEER) ? 2 : 1;
     const int H = nsub * R;
     const int T_out = tile.count;
     const int nq = T_out + 2 * H;       // cells of Q' on chip
     const int Wn = nq + 1 + 2 * HR;     // source cells on chip
-    const long long K = s_K;
-    const bool whole = (s_f == 0.0);    // whole-cell shift: a cyclic permutation
+    const long long K = P.K;
+    const bool whole = P.whole != 0;    // whole-cell shift: a cyclic permutation
     const T *qin = static_cast<const T *>(a.q_in) + row.cell_off;
     T *qout = static_cast<T *>(a.q_out) + row.cell_off;
 
@@ -114,14 +80,15 @@ __global__ void __launch_bounds__(1024) k_uniform(StepArgs a, int tile_cap)
                     sl = vl_slope_u(sQ[w - 1], q0, sQ[w + 1]);
                 else
                     sl = T(0.5) * (sQ[w + 1] - sQ[w - 1]);
-                g = q0 * s_c[0] + sl * s_c[1];
+                g = q0 * P.c[0] + sl * P.c[1];
             } else if (ORDER == 3) {
                 T QL, QR, Q6;
                 ppm_u(sQ[w - 2], sQ[w - 1], sQ[w], sQ[w + 1], sQ[w + 2], lim, QL, QR, Q6);
-                g = QL * s_c[0] + QR * s_c[1] + Q6 * s_c[2];
+                (void)Q6;  // folded: Q6 = 6Q - 3(QL + QR)
+                g = QL * P.c[0] + QR * P.c[1] + sQ[w] * P.c[2];
             } else {
-                g = s_c[0] * sQ[w - 2] + s_c[1] * sQ[w - 1] + s_c[2] * sQ[w] +
-                    s_c[3] * sQ[w + 1] + s_c[4] * sQ[w + 2];
+                g = P.c[0] * sQ[w - 2] + P.c[1] * sQ[w - 1] + P.c[2] * sQ[w] +
+                    P.c[3] * sQ[w + 1] + P.c[4] * sQ[w + 2];
             }
             sA[w] = g;
         }
@@ -138,8 +105,16 @@ __global__ void __launch_bounds__(1024) k_uniform(StepArgs a, int tile_cap)
     if (residual) {
         const T *dv = static_cast<const T *>(a.dv) + row.cell_off;
         const int v0i = wrap_index((int64_t)tile.start - H, N);
-        for (int j = tid; j <= nq; j += nth) sV[j] = dv[(v0i + j) % N];
-        const T cf = (T)(a.dt / nsub / row.dx);  // Courant number per unit dv
+        if (nq < N) {
+            for (int j = tid; j <= nq; j += nth) {
+                int c = v0i + j;
+                if (c >= N) c -= N;
+                sV[j] = dv[c];
+            }
+        } else {
+            for (int j = tid; j <= nq; j += nth) sV[j] = dv[(v0i + j) % N];
+        }
+        const T cf = P.cf;  // Courant number per unit dv
         const bool vl = (a.scheme == RAM_VANLEER);
         __syncthreads();
         for (int k = 0; k < nsub; ++k) {
@@ -176,28 +151,63 @@ __global__ void __launch_bounds__(1024) k_uniform(StepArgs a, int tile_cap)
 }
 
 template <typename T, int ORDER>
-cudaError_t launch_order(const Plan &p, const StepArgs &a0, cudaStream_t s)
+cudaError_t launch_tiles(const Plan &p, const StepArgs &a0, cudaStream_t s, const Tile *tiles,
+                         const std::vector<Tile> &tiles_h)
 {
-    const int n = (int)p.tiles_uniform_h[ORDER].size();
+    const int n = (int)tiles_h.size();
     if (n == 0) return cudaSuccess;
     StepArgs a = a0;
-    a.tiles = p.tiles_uniform[ORDER];
+    a.tiles = tiles;
     a.n_tiles = n;
     int cap = 0;
-    for (const Tile &t : p.tiles_uniform_h[ORDER]) cap = cap > t.count ? cap : t.count;
+    for (const Tile &t : tiles_h) cap = cap > t.count ? cap : t.count;
     constexpr int HR = (ORDER == 2) ? 1 : 2;
     const size_t wcap = cap + 2 * kMaxHalo + 1 + 2 * HR;
     const size_t qcap = cap + 2 * kMaxHalo + 1;
     const size_t smem = sizeof(T) * (2 * wcap + 4 * qcap);
-    cudaError_t e = cudaFuncSetAttribute(k_uniform<T, ORDER>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // raise the dynamic shared-memory limit once per device and size
+    static size_t configured[64] = {0};
+    const int dev = p.device < 64 ? p.device : 63;
+    if (smem > configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_uniform<T, ORDER>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = smem;
+    }
+    return launch_pdl(k_uniform<T, ORDER>, n, p.threads, smem, s, a, cap,
+                      static_cast<const RowParams<T> *>(p.row_par));
+}
+
+bool aligned16(const void *ptr) { return ptr == nullptr || ((uintptr_t)ptr % 16) == 0; }
+
+template <typename T, int ORDER>
+cudaError_t launch_order(const Plan &p, const StepArgs &a, cudaStream_t s)
+{
+    const int d = sizeof(T) == 4 ? 0 : 1;
+    const ram_dtype dt = sizeof(T) == 4 ? RAM_F32 : RAM_F64;
+    // both row kernels read 16-byte vectors (or TMA bulk copies)
+    const bool vec_ok = aligned16(a.q_in) && aligned16(a.dv) && aligned16(a.q_out);
+    if (!vec_ok)
+        return launch_tiles<T, ORDER>(p, a, s, p.tiles_uniform[ORDER], p.tiles_uniform_h[ORDER]);
+    if (p.uniform_kernel[d] == 1 && !p.rows_seg_h[d][ORDER].empty()) {
+        cudaError_t e = launch_useg(p, dt, a, s, ORDER, p.rows_seg[d][ORDER],
+                                    (int)p.rows_seg_h[d][ORDER].size());
+        if (e != cudaSuccess) return e;
+        return launch_tiles<T, ORDER>(p, a, s, p.tiles_rest_seg[d][ORDER],
+                                      p.tiles_rest_seg_h[d][ORDER]);
+    }
+    if (p.rows_fit_h[d][ORDER].empty())
+        return launch_tiles<T, ORDER>(p, a, s, p.tiles_uniform[ORDER], p.tiles_uniform_h[ORDER]);
+    cudaError_t e = launch_rows(p, dt, a, s, ORDER, p.rows_fit[d][ORDER],
+                                (int)p.rows_fit_h[d][ORDER].size(), p.ncap_fit[d][ORDER]);
     if (e != cudaSuccess) return e;
-    k_uniform<T, ORDER><<<n, p.threads, smem, s>>>(a, cap);
-    return cudaGetLastError();
+    return launch_tiles<T, ORDER>(p, a, s, p.tiles_rest[d][ORDER], p.tiles_rest_h[d][ORDER]);
 }
 
 }  // namespace
+
+int rows_kernel_max_cells(ram_dtype dt) { return dt == RAM_F32 ? 12288 : 6144; }
 
 cudaError_t launch_uniform(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s)
 {

@@ -28,7 +28,8 @@ MAX_NSUB = 8
 
 EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwind",
            "ram_step", "ram_step_adjoint", "ram_row_mass", "ram_plan_check_errors",
-           "ram_plan_query", "ram_plan_set_tiling", "ram_status_string", "ram_version"]
+           "ram_plan_query", "ram_plan_set_tiling", "ram_plan_get_tuning",
+           "ram_plan_set_tuning", "ram_plan_autotune", "ram_status_string", "ram_version"]
 
 
 class RamError(RuntimeError):
@@ -51,6 +52,16 @@ class PlanInfo(ctypes.Structure):
                 ("n_uniform_rows", ctypes.c_int32), ("n_tiles_uniform", ctypes.c_int32),
                 ("n_tiles_general", ctypes.c_int32), ("tile_cells", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("rows_cells_per_thread_f32", ctypes.c_int32),
+                ("rows_cells_per_thread_f64", ctypes.c_int32),
+                ("tile_cells", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("uniform_kernel_f32", ctypes.c_int32), ("uniform_kernel_f64", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 _lib = None
@@ -78,6 +89,9 @@ def load(path: Optional[str] = None):
     lib.ram_plan_check_errors.argtypes = [vp]
     lib.ram_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.ram_plan_set_tiling.argtypes = [vp, i32, i32]
+    lib.ram_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    lib.ram_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    lib.ram_plan_autotune.argtypes = [vp, i32, vp, vp, vp, f64, vp, i32, vp, i32, vp]
     lib.ram_status_string.argtypes = [i32]
     lib.ram_status_string.restype = ctypes.c_char_p
     lib.ram_version.restype = i32
@@ -184,6 +198,16 @@ class Plan:
         _check(self._lib.ram_plan_set_tiling(self.handle, int(tile_cells), int(threads)),
                "ram_plan_set_tiling")
 
+    def tuning(self) -> Tuning:
+        out = Tuning()
+        _check(self._lib.ram_plan_get_tuning(self.handle, ctypes.byref(out)),
+               "ram_plan_get_tuning")
+        return out
+
+    def set_tuning(self, t: Tuning):
+        _check(self._lib.ram_plan_set_tuning(self.handle, ctypes.byref(t)),
+               "ram_plan_set_tuning")
+
     def check_errors(self) -> int:
         """Synchronise and return (and clear) the device error status (0 = ok)."""
         return int(self._lib.ram_plan_check_errors(self.handle))
@@ -222,6 +246,17 @@ def step_adjoint(plan: Plan, q_in, g_out, g_in, v0, dt: float, dv=None, g_dv=Non
                                       _ptr(dv), _ptr(g_dv), _ptr(nsub),
                                       _stream(plan.device, stream)),
            "ram_step_adjoint")
+
+
+def autotune(plan: Plan, q_in, q_out, v0, dt: float, dv=None, scheme: int = VANLEER,
+             nsub=None, reps: int = 20, stream=None) -> Tuning:
+    """ram_plan_autotune: time the candidate launch shapes on these buffers and keep
+    the fastest in the plan."""
+    _check(plan._lib.ram_plan_autotune(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
+                                       _ptr(v0), float(dt), _ptr(dv), int(scheme), _ptr(nsub),
+                                       int(reps), _stream(plan.device, stream)),
+           "ram_plan_autotune")
+    return plan.tuning()
 
 
 def row_mass(plan: Plan, q, out, stream=None):

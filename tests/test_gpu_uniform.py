@@ -225,3 +225,129 @@ def test_full_size_disk_sampled():
             err = np.sum(np.abs(out[sl] - ref[sl])) / np.sum(np.abs(ref[sl]))
             assert err <= TOL[dtype], (dtype, r, err)
     assert plan.check_errors() == 0
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_uniform_rows_of_mixed_lengths(dtype):
+    """Uniform rows of different lengths in one plan: lengths that the persistent
+    whole-row kernel takes (16-byte aligned, up to its shared-memory cap, partial
+    last groups) and lengths that go to the tiled kernel, with per-row shifts and
+    sub-step counts."""
+    lens = [16, 20, 64, 1000, 1024, 4096, 5000, 12288, 13000, 7]
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nodes = np.concatenate([wl.uniform_nodes(n, -0.5, 1.0 + 0.1 * r) for r, n in enumerate(lens)])
+    rng = np.random.default_rng(5)
+    q0 = 1.0 + rng.random(int(ro[-1]))
+    dv = 0.2 * (rng.random(int(ro[-1])) - 0.5)
+    plan = ram.Plan(ro, nodes, order=3, limiter=True)
+    dt = 0.01
+    v0 = rng.uniform(-30.0, 30.0, len(lens))
+    nsub = np.array([1 + (r % 3) for r in range(len(lens))], dtype=np.int32)
+    # keep |dv| dt / (nsub dx) <= 1: dx = L / n
+    for r, n in enumerate(lens):
+        L = 1.0 + 0.1 * r
+        dv[ro[r]:ro[r + 1]] *= min(1.0, 0.9 * nsub[r] * (L / n) / (0.1 * dt))
+    qd = _t(q0, DT[dtype])
+    out = torch.empty_like(qd)
+    dvd = _t(dv, DT[dtype])
+    ram.step(plan, qd, out, _t(v0, torch.float64), dt, dv=dvd, scheme=ram.VANLEER,
+             nsub=_t(nsub, torch.int32))
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    qr = qd.double().cpu().numpy()
+    dvr = dvd.double().cpu().numpy()
+    for r, n in enumerate(lens):
+        sl = slice(int(ro[r]), int(ro[r + 1]))
+        x = nodes[ro[r] + r: ro[r + 1] + r + 1]
+        ref = oracle.step(x, qr[sl], oracle.shift_from_velocity(v0[r], dt), 3, True, dvr[sl],
+                          dt, oracle.VANLEER, int(nsub[r]))
+        err = np.sum(np.abs(got[sl] - ref)) / np.sum(np.abs(ref))
+        assert err <= TOL[dtype], (n, err)
+    assert plan.check_errors() == 0
+
+
+def test_misaligned_arrays_take_the_tiled_path():
+    """Arrays that are not 16-byte aligned cannot be read with TMA; the launcher
+    falls back to the tiled kernel and the result is the same."""
+    w = wl.disk(n_r=4, n_phi=512)
+    plan = ram.Plan.from_workload(w)
+    base = torch.zeros(w.n_cells + 1, dtype=torch.float32, device=DEV)
+    qa = base[1:]
+    qa.copy_(_t(w.q0, torch.float32))
+    qb = _t(w.q0, torch.float32)
+    dvd = _t(w.dv, torch.float32)
+    v0 = _t(w.v0, torch.float64)
+    ns = _t(w.nsub, torch.int32)
+    oa, ob = torch.empty_like(qb), torch.empty_like(qb)
+    ram.step(plan, qa, oa, v0, w.dt, dv=dvd, scheme=ram.VANLEER, nsub=ns)
+    ram.step(plan, qb, ob, v0, w.dt, dv=dvd, scheme=ram.VANLEER, nsub=ns)
+    torch.cuda.synchronize()
+    err = float((oa.double() - ob.double()).abs().sum() / ob.double().abs().sum())
+    assert err <= 1e-6
+
+
+def test_autotune_and_tuning_roundtrip():
+    """The autotuner keeps a valid candidate; every launch shape gives the same
+    result within round-off."""
+    w = wl.disk(n_r=16, n_phi=2048)
+    plan = ram.Plan.from_workload(w)
+    q = _t(w.q0, torch.float32)
+    dvd = _t(w.dv, torch.float32)
+    v0 = _t(w.v0, torch.float64)
+    ns = _t(w.nsub, torch.int32)
+    outs = []
+    for v in (5, 7, 9, 11, 15):
+        t = plan.tuning()
+        t.rows_cells_per_thread_f32 = v
+        plan.set_tuning(t)
+        o = torch.empty_like(q)
+        ram.step(plan, q, o, v0, w.dt, dv=dvd, scheme=ram.VANLEER, nsub=ns)
+        outs.append(o)
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        assert torch.allclose(o, outs[0], rtol=1e-6, atol=1e-7)
+    t = ram.autotune(plan, q, torch.empty_like(q), v0, w.dt, dv=dvd, scheme=ram.VANLEER,
+                     nsub=ns, reps=3)
+    assert t.rows_cells_per_thread_f32 in (5, 7, 9, 11, 15)
+    assert plan.check_errors() == 0
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+@pytest.mark.parametrize("scheme,nsub_max", [(ram.VANLEER, 8), (ram.DONOR, 8), (ram.VANLEER, 1)])
+def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
+    """The warp-segment kernel and the persistent whole-row kernel against the
+    oracle, with sub-step counts up to the maximum (widest warp halos) and rows
+    long enough for several warp segments."""
+    n_r, n_phi = 6, 2048
+    x = wl.uniform_nodes(n_phi, 0.0, 2 * np.pi)
+    rng = np.random.default_rng(21)
+    q0 = 1.0 + rng.random(n_r * n_phi)
+    nsub = np.array([1 + (r * 3) % nsub_max for r in range(n_r)], dtype=np.int32)
+    dt = 0.5
+    dxc = 2 * np.pi / n_phi
+    dv = (rng.random(n_r * n_phi) - 0.5) * 1.6 * dxc / dt
+    dv *= np.repeat(nsub, n_phi) / nsub_max  # |dv| dt / (nsub dx) <= 0.8 / nsub_max
+    v0 = rng.uniform(-400.0, 400.0, n_r) * dxc / dt
+    ro = np.arange(n_r + 1, dtype=np.int64) * n_phi
+    plan = ram.Plan(ro, x, order=3, shared_mesh=True)
+    qd, dvd = _t(q0, DT[dtype]), _t(dv, DT[dtype])
+    qr, dvr = qd.double().cpu().numpy(), dvd.double().cpu().numpy()
+    refs = np.concatenate([oracle.step(x, qr[r * n_phi:(r + 1) * n_phi],
+                                       oracle.shift_from_velocity(v0[r], dt), 3, True,
+                                       dvr[r * n_phi:(r + 1) * n_phi], dt, scheme, int(nsub[r]))
+                           for r in range(n_r)])
+    for kern in (0, 1):
+        t = plan.tuning()
+        t.uniform_kernel_f32 = kern
+        t.uniform_kernel_f64 = kern
+        plan.set_tuning(t)
+        out = torch.empty_like(qd)
+        ram.step(plan, qd, out, _t(v0, torch.float64), dt, dv=dvd, scheme=scheme,
+                 nsub=_t(nsub, torch.int32))
+        torch.cuda.synchronize()
+        got = out.double().cpu().numpy()
+        for r in range(n_r):
+            sl = slice(r * n_phi, (r + 1) * n_phi)
+            err = np.sum(np.abs(got[sl] - refs[sl])) / np.sum(np.abs(refs[sl]))
+            assert err <= TOL[dtype], (kern, r, err)
+    assert plan.check_errors() == 0
