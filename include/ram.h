@@ -184,6 +184,36 @@ ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, v
                              ram_scheme scheme, const int32_t *nsub, int32_t reps,
                              void *stream);
 
+/* Largest number of rows ram_step_uniform_noalloc accepts. */
+#define RAM_STATIC_MAX_ROWS 4096
+
+/* One RAM step that allocates no device memory, for callers that cannot call
+ * cudaMalloc (code running inside an allocator or memory-pool callback, or
+ * next to a fixed device-memory budget that must not move).  The paper has no
+ * counterpart: it is a plan-free variant of ram_step for n_rows rows of
+ * n_cells_per_row cells each, packed back to back, all on one uniform periodic
+ * mesh of period `period` (the rings of a disk), with reconstruction `order`
+ * (2, 3, 4) and flags 0 or RAM_LIMITER_OFF.  The other arguments are those of
+ * ram_step (no phase).  Its row table, row list and per-row shift parameters
+ * live in one static device array of about 0.6 MiB that every GPU loading the
+ * library keeps until the process exits; rows beyond RAM_STATIC_MAX_ROWS are
+ * refused with RAM_ERR_ARG.  Rows must have at least 512 cells and a multiple
+ * of 16 bytes per row, and q_in, q_out and dv_iface must be 16-byte aligned
+ * (RAM_ERR_UNSUPPORTED / RAM_ERR_ARG otherwise).
+ * Device-side conditions (CFL, non-finite shift, sub-step count) are ORed into
+ * *device_errors (device int32, bits as in the plan error word: 1 CFL,
+ * 2 non-finite, 4 sub-step count) when it is not NULL; the caller clears it.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  Every call overwrites the array, so calls whose kernels overlap on
+ * the GPU (other streams, other threads) race; order them on one stream. */
+ram_status ram_step_uniform_noalloc(ram_dtype dtype, int32_t n_rows, int32_t n_cells_per_row,
+                                    double period, int32_t order, uint32_t flags,
+                                    const void *q_in, void *q_out, const double *v0,
+                                    double dt, const void *dv_iface, ram_scheme scheme,
+                                    const int32_t *nsub, int32_t *device_errors,
+                                    void *stream);
+
 const char *ram_status_string(ram_status status);
 
 /* Library version, major * 10000 + minor * 100 + patch. */

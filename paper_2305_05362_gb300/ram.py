@@ -29,7 +29,9 @@ MAX_NSUB = 8
 EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwind",
            "ram_step", "ram_step_adjoint", "ram_row_mass", "ram_plan_check_errors",
            "ram_plan_query", "ram_plan_set_tiling", "ram_plan_get_tuning",
-           "ram_plan_set_tuning", "ram_plan_autotune", "ram_status_string", "ram_version"]
+           "ram_plan_set_tuning", "ram_plan_autotune", "ram_step_uniform_noalloc",
+           "ram_status_string", "ram_version"]
+STATIC_MAX_ROWS = 4096
 
 
 class RamError(RuntimeError):
@@ -92,6 +94,8 @@ def load(path: Optional[str] = None):
     lib.ram_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.ram_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.ram_plan_autotune.argtypes = [vp, i32, vp, vp, vp, f64, vp, i32, vp, i32, vp]
+    lib.ram_step_uniform_noalloc.argtypes = [i32, i32, i32, f64, i32, ctypes.c_uint32, vp, vp,
+                                             vp, f64, vp, i32, vp, vp, vp]
     lib.ram_status_string.argtypes = [i32]
     lib.ram_status_string.restype = ctypes.c_char_p
     lib.ram_version.restype = i32
@@ -263,6 +267,22 @@ def row_mass(plan: Plan, q, out, stream=None):
     """ram_row_mass: per-row mass (FP64) into out."""
     _check(plan._lib.ram_row_mass(plan.handle, _dtype_code(q), _ptr(q), _ptr(out),
                                   _stream(plan.device, stream)), "ram_row_mass")
+
+
+def step_uniform_noalloc(q_in, q_out, n_rows: int, period: float, order: int, v0, dt: float,
+                         dv=None, scheme: int = VANLEER, nsub=None, limiter: bool = True,
+                         device_errors=None, stream=None):
+    """ram_step_uniform_noalloc: one step of n_rows equal uniform rows without any
+    device allocation (the library's static scratch array holds its tables)."""
+    lib = load()
+    n_cells = q_in.numel() // n_rows
+    dev = q_in.device.index if q_in.device.index is not None else 0
+    _check(lib.ram_step_uniform_noalloc(_dtype_code(q_in), int(n_rows), int(n_cells),
+                                        float(period), int(order),
+                                        0 if limiter else LIMITER_OFF, _ptr(q_in), _ptr(q_out),
+                                        _ptr(v0), float(dt), _ptr(dv), int(scheme), _ptr(nsub),
+                                        _ptr(device_errors), _stream(dev, stream)),
+           "ram_step_uniform_noalloc")
 
 
 def version() -> int:
