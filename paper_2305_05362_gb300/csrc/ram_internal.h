@@ -77,7 +77,9 @@ template <typename T> struct RowParams {
     int32_t whole;     // the shift is a whole number of cells
     int32_t nsub;      // residual sub-steps (0: no residual in this launch)
     T c[5];            // partial-integral coefficients at the edge offset
-    T cf;              // Courant number per unit dv of one sub-step
+    T cf;              // uniform rows: Courant number per unit dv of one sub-step;
+                       // other rows: the sub-step length dt / nsub
+    uint64_t sfix;     // the shift as a fraction of the period in units of 2^-64
 };
 
 // the plan

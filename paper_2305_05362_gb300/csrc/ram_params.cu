@@ -28,7 +28,6 @@ __global__ void __launch_bounds__(128) k_params(StepArgs a, int n_rows, RowParam
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rows) return;
     const RowInfo row = a.rows[r];
-    if (!row.uniform) return;
     const int N = row.n;
     RowParams<T> P;
     P.cell_off = row.cell_off;
@@ -36,7 +35,15 @@ __global__ void __launch_bounds__(128) k_params(StepArgs a, int n_rows, RowParam
     const double sft = row_shift(a, r);
     if (a.mode == MODE_STEP && a.phase != nullptr)
         a.phase[r] = reduce_mod_rcp(a.phase[r] + sft, row.period, row.inv_period);
-    double sig = reduce_mod_rcp(sft, row.period, row.inv_period) * row.cells_per_length;
+    const double sred = reduce_mod_rcp(sft, row.period, row.inv_period);
+    // fixed-point shift for rows with their own mesh: nodes are stored as fractions
+    // of the period in units of 2^-64, so x - s and the periodic wrap are exact
+    // integer arithmetic
+    {
+        const double t = sred * row.inv_period;  // in [0, 1]
+        P.sfix = (t >= 1.0) ? 0ull : __double2ull_rn(t * 18446744073709551616.0);
+    }
+    double sig = sred * row.cells_per_length;
     if (sig >= (double)N) sig -= (double)N;
     const double Kd = floor(sig);
     const double f = sig - Kd;
@@ -67,7 +74,8 @@ __global__ void __launch_bounds__(128) k_params(StepArgs a, int n_rows, RowParam
             atomicOr(a.err, ERR_NSUB);
             nsub = nsub < 1 ? 1 : RAM_MAX_NSUB;
         }
-        P.cf = (T)(a.dt * row.cells_per_length * inv_small(nsub));
+        P.cf = row.uniform ? (T)(a.dt * row.cells_per_length * inv_small(nsub))
+                           : (T)(a.dt * inv_small(nsub));
     }
     P.nsub = nsub;
     out[r] = P;
@@ -77,7 +85,6 @@ __global__ void __launch_bounds__(128) k_params(StepArgs a, int n_rows, RowParam
 
 cudaError_t launch_params(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s)
 {
-    if (p.n_uniform_rows == 0) return cudaSuccess;
     const int threads = 128;
     const int blocks = (p.n_rows + threads - 1) / threads;
     if (dt == RAM_F32)

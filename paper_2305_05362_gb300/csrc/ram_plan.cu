@@ -128,25 +128,16 @@ ram_status build_tiles(Plan &p)
     }
     p.window_max = 0;
     const int halo_res = 2 * RAM_MAX_NSUB;  // residual halo, cells per side
+    const int tg = std::max(64, p.tile_cells / 2);  // output cells per non-uniform tile
     for (int r = 0; r < p.n_rows; ++r) {
         const RowInfo &ri = p.rows_h[r];
         const int n = ri.n;
-        const int nt = (n + p.tile_cells - 1) / p.tile_cells;
-        const bool uni = ri.uniform != 0;
-        // per-row mesh for the window bound
-        const double *x = nullptr;
-        std::vector<double> w2;
-        if (!uni) {
-            x = (p.flags & RAM_SHARED_MESH) ? p.nodes_h.data()
-                                            : p.nodes_h.data() + p.row_offset[r] + r;
-            w2.resize(2 * (size_t)n);
-            for (int i = 0; i < n; ++i) w2[i] = w2[i + n] = x[i + 1] - x[i];
-        }
-        for (int t = 0; t < nt; ++t) {
-            int a = (int)((int64_t)n * t / nt);
-            int b = (int)((int64_t)n * (t + 1) / nt);
-            Tile tl{r, a, b - a, 0};
-            if (uni) {
+        if (ri.uniform) {
+            const int nt = (n + p.tile_cells - 1) / p.tile_cells;
+            for (int t = 0; t < nt; ++t) {
+                const int a = (int)((int64_t)n * t / nt);
+                const int b = (int)((int64_t)n * (t + 1) / nt);
+                const Tile tl{r, a, b - a, 0};
                 p.tiles_uniform_h[ri.order].push_back(tl);
                 // persistent whole-row kernel: TMA needs 16-byte aligned row starts and
                 // lengths, and the row (plus halos) must fit the shared-memory stages
@@ -172,38 +163,47 @@ ram_status build_tiles(Plan &p)
                         p.tiles_rest_seg_h[d][ri.order].push_back(tl);
                     }
                 }
-            } else {
-                // physical length of the output cells [a - halo, b + halo) (cyclic)
-                int span = std::min(n, (b - a) + 2 * halo_res);
-                double len = 0.0;
-                int first = ((a - halo_res) % n + n) % n;
-                for (int k = 0; k < span; ++k) len += w2[first + k];
-                // max number of source cells intersecting an interval of length len
-                int best = 0;
-                if (span >= n) {
-                    best = n + 1;
-                } else {
-                    // two pointers over the doubled width list: for each start cell i,
-                    // cells i..j-1 are covered while their summed width is < len
-                    double acc = 0.0;
-                    int j = 0;
-                    for (int i = 0; i < n; ++i) {
-                        if (j < i) {
-                            j = i;
-                            acc = 0.0;
-                        }
-                        while (j < i + n && acc + w2[j] < len) acc += w2[j++];
-                        // an interval of length len starting inside cell i touches at
-                        // most cells i .. j+1
-                        best = std::max(best, j - i + 2);
-                        if (j > i) acc -= w2[i];
-                    }
-                    best = std::min(best, n + 1);
-                }
-                tl.window = best + 2 * 2 + 2;  // reconstruction halo (2 per side) + slack
-                p.window_max = std::max(p.window_max, tl.window);
-                p.tiles_general_h[ri.order].push_back(tl);
             }
+            continue;
+        }
+        // non-uniform row: one cyclic tile for short rows, else windowed tiles
+        if (n <= 2 * tg + 4 * halo_res) {
+            p.tiles_general_h[ri.order].push_back(Tile{r, 0, n, 0});
+            continue;
+        }
+        const double *x = (p.flags & RAM_SHARED_MESH) ? p.nodes_h.data()
+                                                       : p.nodes_h.data() + p.row_offset[r] + r;
+        std::vector<double> w2(2 * (size_t)n);
+        for (int i = 0; i < n; ++i) w2[i] = w2[i + n] = x[i + 1] - x[i];
+        const int nt = (n + tg - 1) / tg;
+        for (int t = 0; t < nt; ++t) {
+            const int a = (int)((int64_t)n * t / nt);
+            const int b = (int)((int64_t)n * (t + 1) / nt);
+            Tile tl{r, a, b - a, 0};
+            // physical length of the output cells [a - halo, b + halo) (cyclic)
+            const int span = (b - a) + 2 * halo_res;
+            double len = 0.0;
+            const int first = ((a - halo_res) % n + n) % n;
+            for (int k = 0; k < span; ++k) len += w2[(first + k) % (2 * n)];
+            // most source cells an interval of that length can touch: for every
+            // start s, cells s..e-1 fit strictly inside it; it also touches cell e
+            // and the cell s-1 it may start in
+            int best = 0;
+            double acc = 0.0;
+            int e = 0;
+            for (int st = 0; st < n; ++st) {
+                if (e < st) {
+                    e = st;
+                    acc = 0.0;
+                }
+                while (e < st + n && acc + w2[e] < len) acc += w2[e++];
+                best = std::max(best, e - st + 2);
+                if (e > st) acc -= w2[st];
+            }
+            best = std::min(best, n + 1);
+            tl.window = best + 2 * 2 + 2;  // reconstruction halo (2 per side) + slack
+            p.window_max = std::max(p.window_max, tl.window);
+            p.tiles_general_h[ri.order].push_back(tl);
         }
     }
     for (int o = 2; o <= 4; ++o) {

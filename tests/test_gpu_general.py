@@ -1,0 +1,209 @@
+"""GPU parity of the non-uniform-mesh path against the FP64 oracle, through the C
+ABI: FP64 relative L1 <= 1e-12, FP32 <= 1e-5 (per row)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2305_05362_gb300 import ram, workloads as wl
+from gpu_common import TOL, oracle_shifts, oracle_step, rel_l1_rows
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+DT = {"float64": torch.float64, "float32": torch.float32}
+
+
+def _t(a, dtype):
+    return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def _rounded(a, dtype):
+    a = np.asarray(a, dtype=np.float64)
+    return a.astype(np.float32).astype(np.float64) if dtype == "float32" else a
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_line_nonuniform_c2(dtype):
+    """4096 cells, log-uniform widths in [0.5, 2] x mean, three Gaussians, 40.7 mean
+    cells per step, dv = 0.05 sin(4 pi x), PPM + van Leer: after 1 and 20 steps."""
+    w = wl.line_nonuniform()
+    plan = ram.Plan.from_workload(w)
+    assert plan.info().n_uniform_rows == 0
+    q = _t(w.q0, DT[dtype])
+    buf = torch.empty_like(q)
+    dvd = _t(w.dv, DT[dtype])
+    v0 = _t(w.v0, torch.float64)
+    ref = q.double().cpu().numpy()
+    dvr = dvd.double().cpu().numpy()
+    shifts = oracle_shifts(w)
+    for k in range(1, 21):
+        ram.step(plan, q, buf, v0, w.dt, dv=dvd, scheme=ram.VANLEER)
+        q, buf = buf, q
+        ref = oracle_step(w, ref, shifts, dv=dvr, nsub=w.nsub)
+        if k in (1, 20):
+            torch.cuda.synchronize()
+            err = rel_l1_rows(w, q.double().cpu().numpy(), ref)
+            assert err <= TOL[dtype] * k, (k, err)
+    assert plan.check_errors() == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 40, 333, 1500, 4001])
+@pytest.mark.parametrize("ratio", [1.5, 16.0])
+@pytest.mark.parametrize("order,limiter", [(2, True), (2, False), (3, True), (3, False),
+                                           (4, False)])
+def test_random_meshes(n, ratio, order, limiter):
+    """Random non-uniform rows from a single cell to several windowed tiles, strongly
+    varying widths, shifts of many periods both ways, residual included; FP64."""
+    x = wl.random_nodes(n, seed=n + int(ratio), ratio=ratio, x0=-0.25)
+    rng = np.random.default_rng(n)
+    q0 = 1.0 + rng.random(n)
+    dxmin = np.diff(x).min()
+    dt = 0.1
+    dv = (rng.random(n) - 0.5) * 1.2 * dxmin / dt  # |dv| dt <= 0.6 dx_min
+    plan = ram.Plan([0, n], x, order=order, limiter=limiter)
+    plan.set_tiling(512, 128)  # non-uniform tiles of 256 cells: rows > ~600 are windowed
+    qd, dvd = _t(q0, torch.float64), _t(dv, torch.float64)
+    for s in (0.0, 0.3 * dxmin, 0.4321, 7.77, -3.1415):
+        out = torch.empty_like(qd)
+        v0 = _t([s / dt], torch.float64)
+        ram.step(plan, qd, out, v0, dt, dv=dvd, scheme=ram.VANLEER)
+        torch.cuda.synchronize()
+        ref = oracle.step(x, q0, oracle.shift_from_velocity(s / dt, dt), order, limiter, dv, dt,
+                          oracle.VANLEER, 1)
+        err = np.sum(np.abs(out.cpu().numpy() - ref)) / np.sum(np.abs(ref))
+        assert err <= 1e-12, (s, err)
+    assert plan.check_errors() == 0
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_long_row_windowed_tiles(dtype, order):
+    """A 20000-cell row in tiles of 256 output cells: every tile locates its own source
+    window through the bucket table; shift only and full step."""
+    n = 20000
+    x = wl.random_nodes(n, seed=77)
+    q0 = _rounded(wl.three_gaussians(x, 78), dtype)
+    plan = ram.Plan([0, n], x, order=order, limiter=(order != 4))
+    plan.set_tiling(512, 256)
+    assert plan.info().n_tiles_general > 20
+    qd = _t(q0, DT[dtype])
+    out = torch.empty_like(qd)
+    for s in (123.4 / n, 0.5, 2.0 + 17.3 / n):
+        ram.shift(plan, qd, out, _t([s], torch.float64))
+        torch.cuda.synchronize()
+        ref = oracle.shift(x, q0, s, order, order != 4)
+        err = np.sum(np.abs(out.double().cpu().numpy() - ref)) / np.sum(np.abs(ref))
+        assert err <= TOL[dtype], (s, err)
+    assert plan.check_errors() == 0
+
+
+def test_full_period_identity_nonuniform():
+    """A shift by whole periods returns the input bit for bit on a non-uniform mesh
+    (every shifted edge lands exactly on its own node: the exact-cover copy)."""
+    for n in (5, 600, 3000):
+        x = wl.random_nodes(n, seed=n)
+        plan = ram.Plan([0, n], x, order=3)
+        for dtype in (torch.float64, torch.float32):
+            q = torch.rand(n, dtype=dtype, device=DEV) + 0.5
+            out = torch.empty_like(q)
+            for m in (1.0, 3.0, -2.0):
+                ram.shift(plan, q, out, _t([m], torch.float64))
+                torch.cuda.synchronize()
+                assert torch.equal(out, q), (n, dtype, m)
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_mixed_uniform_and_nonuniform_rows(dtype):
+    """One plan with uniform and non-uniform rows of assorted lengths and orders."""
+    lens = [700, 64, 2048, 9, 1500, 4096]
+    uni = [True, False, True, False, False, True]
+    orders = np.array([3, 2, 4, 3, 4, 2], dtype=np.int8)
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nodes = np.concatenate([wl.uniform_nodes(n) if u else wl.random_nodes(n, seed=r)
+                            for r, (n, u) in enumerate(zip(lens, uni))])
+    rng = np.random.default_rng(9)
+    q0 = _rounded(1.0 + rng.random(int(ro[-1])), dtype)
+    dt = 0.2
+    dv = np.concatenate([(rng.random(n) - 0.5) * 0.5 / n / dt for n in lens])
+    dv = _rounded(dv, dtype)
+    v0 = rng.uniform(-5, 5, len(lens)) / dt
+    plan = ram.Plan(ro, nodes, order=orders, limiter=False)
+    info = plan.info()
+    assert info.n_uniform_rows == 3
+    qd, dvd = _t(q0, DT[dtype]), _t(dv, DT[dtype])
+    out = torch.empty_like(qd)
+    ram.step(plan, qd, out, _t(v0, torch.float64), dt, dv=dvd, scheme=ram.DONOR)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    for r, n in enumerate(lens):
+        sl = slice(int(ro[r]), int(ro[r + 1]))
+        x = nodes[ro[r] + r: ro[r + 1] + r + 1]
+        ref = oracle.step(x, q0[sl], oracle.shift_from_velocity(v0[r], dt), int(orders[r]), False,
+                          dv[sl], dt, oracle.DONOR, 1)
+        err = np.sum(np.abs(got[sl] - ref)) / np.sum(np.abs(ref))
+        assert err <= TOL[dtype], (r, err)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_batched_uneven_rows(dtype):
+    """The batched recipe (uneven rows with their own meshes, per-row shifts of
+    0.3-200 mean cells, orders 2/3/4, limiter off), reduced to 40 rows of up to 8192
+    cells: one step and five steps."""
+    w = wl.batched(n_rows=40, n_max=8192, steps=5)
+    plan = ram.Plan.from_workload(w)
+    q = _t(w.q0, DT[dtype])
+    buf = torch.empty_like(q)
+    v0 = _t(w.v0, torch.float64)
+    ref = q.double().cpu().numpy()
+    shifts = oracle_shifts(w)
+    for k in range(1, w.steps + 1):
+        ram.step(plan, q, buf, v0, w.dt)
+        q, buf = buf, q
+        ref = oracle_step(w, ref, shifts)
+        if k in (1, w.steps):
+            torch.cuda.synchronize()
+            err = rel_l1_rows(w, q.double().cpu().numpy(), ref)
+            assert err <= TOL[dtype] * k, (k, err)
+    assert plan.check_errors() == 0
+
+
+def test_row_mass_compensated_scan():
+    """ram_row_mass uses the kernels' compensated scan: for FP32 cells its total
+    matches the exact sum of the stored FP32 masses to 1e-12 relative; FP64 to 1e-13."""
+    w = wl.batched(n_rows=24, n_min=1000, n_max=65536, seed_len=3)
+    plan = ram.Plan.from_workload(w)
+    q32 = w.q0.astype(np.float32)
+    out = torch.empty(w.n_rows, dtype=torch.float64, device=DEV)
+    ram.row_mass(plan, _t(q32, torch.float32), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for r in range(w.n_rows):
+        sl = w.row_slice(r)
+        dx32 = np.diff(w.row_nodes(r)).astype(np.float32).astype(np.float64)
+        exact = math.fsum((q32[sl].astype(np.float64) * dx32).tolist())
+        assert abs(got[r] - exact) <= 1e-12 * abs(exact), (r, got[r], exact)
+    ram.row_mass(plan, _t(w.q0, torch.float64), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for r in range(w.n_rows):
+        exact = oracle.mass(w.row_nodes(r), w.q0[w.row_slice(r)])
+        assert abs(got[r] - exact) <= 1e-13 * abs(exact)
+
+
+def test_step_conserves_mass_fp64():
+    """Eq. 10 on the GPU: the FP64 step conserves every row's mass to round-off."""
+    w = wl.batched(n_rows=16, n_max=20000, seed_len=12)
+    plan = ram.Plan.from_workload(w)
+    q = _t(w.q0, torch.float64)
+    out = torch.empty_like(q)
+    m0 = torch.empty(w.n_rows, dtype=torch.float64, device=DEV)
+    m1 = torch.empty_like(m0)
+    ram.row_mass(plan, q, m0)
+    ram.step(plan, q, out, _t(w.v0, torch.float64), w.dt)
+    ram.row_mass(plan, out, m1)
+    torch.cuda.synchronize()
+    rel = ((m1 - m0).abs() / m0.abs()).max().item()
+    assert rel <= 1e-13, rel
