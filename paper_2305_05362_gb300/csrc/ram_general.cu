@@ -573,10 +573,4 @@ cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const Plan &, ram_dtype, const StepArgs &, const void *, void *,
-                           void *, cudaStream_t)
-{
-    return cudaErrorNotSupported;
-}
-
 }  // namespace ram
