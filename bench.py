@@ -140,6 +140,16 @@ def _traffic(kernel_key):
     return ent
 
 
+def _kernel_name(tuning):
+    """The FP32 uniform-row kernel (order 3) the tuning selects, as ncu names it."""
+    k = tuning["uniform_kernel_f32"]
+    if k == 0:
+        return "k_rows<float,3,%d>" % tuning["rows_cells_per_thread_f32"]
+    if k == 1:
+        return "k_useg<float,3,8>"
+    return "k_stream<3,%d>" % tuning["stream_cells_per_lane_f32"]
+
+
 def cpu_baseline(w, budget_s=10.0):
     """The FP64 oracle (C, OpenMP over rows) on the host cores: whole-disk steps
     until the time budget is spent."""
@@ -321,7 +331,7 @@ def main():
     step_s = total_s / args.steps
     achieved = w.n_cells * bpc / step_s / 1e9
     peak, peak_kind = _peaks()
-    kernel_key = "k_uniform<float,3>" if info.n_tiles_general == 0 else "k_general<float>"
+    kernel_key = _kernel_name(tuning) if info.n_tiles_general == 0 else "k_general<float>"
     tr = _traffic(kernel_key + ":" + w.name)
 
     # FP64 form of the same step, and the FP32-vs-FP64 error after the same steps

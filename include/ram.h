@@ -164,8 +164,13 @@ typedef struct {
     int32_t tile_cells;                 /* tiled kernels: output cells per tile */
     int32_t threads;                    /* tiled kernels: threads per CTA */
     int32_t uniform_kernel_f32;         /* uniform rows, FP32: 0 = persistent whole-row
-                                           kernel (TMA-staged rows), 1 = warp segments */
-    int32_t uniform_kernel_f64;         /* the same for FP64 */
+                                           kernel (TMA-staged rows), 1 = warp segments,
+                                           2 = streaming warps (TMA-staged segments) */
+    int32_t uniform_kernel_f64;         /* uniform rows, FP64: 0 or 1 */
+    int32_t rows_ctas_per_sm_f32;       /* whole-row kernel, FP32: CTAs per SM, 1..4 */
+    int32_t rows_ctas_per_sm_f64;       /* whole-row kernel, FP64: 1 */
+    int32_t stream_cells_per_lane_f32;  /* streaming-warp kernel, FP32: 4 or 8 cells per
+                                           lane and segment (8 needs rows >= 520 cells) */
 } ram_tuning;
 
 ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out);
@@ -175,8 +180,10 @@ ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *tuning);
 /* Autotuner: times every candidate launch shape of the kernels this plan uses
  * on the caller's buffers -- the arguments of ram_step, without the phase --
  * with CUDA events on `stream` (`reps` timed steps per candidate) and keeps the
- * fastest in the plan.  Candidates: for uniform rows the warp-segment kernel and
- * the persistent whole-row kernel with cells per thread {5,7,9,11,15}; tile cells
+ * fastest in the plan.  Candidates: for uniform rows the warp-segment kernel,
+ * for FP32 the streaming-warp kernel with 4 or 8 cells per lane, and the
+ * persistent whole-row kernel with (cells per thread, CTAs per SM) in
+ * {5,7,9,11,15} x {2,3,4} as the register budget allows; tile cells
  * {256,512,1024,2048} x threads {128,256} of the tiled kernels.  Host
  * synchronous; overwrites q_out. */
 ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,

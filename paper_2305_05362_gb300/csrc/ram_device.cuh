@@ -151,6 +151,75 @@ __device__ __forceinline__ void quartic_coeffs_u(double xi, double c[5])
     c[4] = w[5];
 }
 
+// The shift parameters of one row for one launch (S0), in FP64: the bulk
+// displacement s (row_shift), the accumulated phase (advanced by s when
+// update_phase), the fixed-point shift of rows with their own mesh, and for
+// uniform rows sig = (s mod L) N / L split into K = floor(sig) whole cells and
+// the fraction f, with the coefficients of the left partial integral at the
+// edge offset xi = 1 - f:
+//   PLM  G/dx = Q xi + slope (xi^2 - xi)/2,
+//   PPM  G/dx = QL (xi - xi^2/2) + QR xi^2/2 + Q6 (xi^2/2 - xi^3/3), folded with
+//        Q6 = 6Q - 3(QL + QR) into coefficients of QL, QR and Q,
+//   order 4: Lagrange weights of the two quartics of the cumulative mass;
+// and cf = dt / (nsub dx), the Courant number per unit dv of one residual
+// sub-step.  Returns xi.  Every kernel that needs these values computes them
+// with this function, so they agree bit for bit.
+template <typename T>
+__device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo &row, int r,
+                                               bool update_phase, RowParams<T> &P)
+{
+    const int N = row.n;
+    P.cell_off = row.cell_off;
+    P.n = N;
+    const double sft = row_shift(a, r);
+    if (update_phase && a.mode == MODE_STEP && a.phase != nullptr)
+        a.phase[r] = reduce_mod_rcp(a.phase[r] + sft, row.period, row.inv_period);
+    const double sred = reduce_mod_rcp(sft, row.period, row.inv_period);
+    // fixed-point shift for rows with their own mesh: nodes are stored as fractions
+    // of the period in units of 2^-64, so x - s and the periodic wrap are exact
+    // integer arithmetic
+    {
+        const double t = sred * row.inv_period;  // in [0, 1]
+        P.sfix = (t >= 1.0) ? 0ull : __double2ull_rn(t * 18446744073709551616.0);
+    }
+    double sig = sred * row.cells_per_length;
+    if (sig >= (double)N) sig -= (double)N;
+    const double Kd = floor(sig);
+    const double f = sig - Kd;
+    P.K = (int)Kd;
+    P.whole = (f == 0.0);
+    const double xi = 1.0 - f;
+    for (int j = 0; j < 5; ++j) P.c[j] = T(0);
+    if (row.order == 2) {
+        P.c[0] = (T)xi;
+        P.c[1] = (T)(0.5 * (xi * xi - xi));
+    } else if (row.order == 3) {
+        const double c0 = xi - 0.5 * xi * xi, c1 = 0.5 * xi * xi;
+        const double c6 = 0.5 * xi * xi - xi * xi * xi * (1.0 / 3.0);
+        P.c[0] = (T)(c0 - 3.0 * c6);
+        P.c[1] = (T)(c1 - 3.0 * c6);
+        P.c[2] = (T)(6.0 * c6);
+    } else {
+        double c[5];
+        quartic_coeffs_u(xi, c);
+        for (int j = 0; j < 5; ++j) P.c[j] = (T)c[j];
+    }
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    int nsub = 0;
+    P.cf = T(0);
+    if (has_dv) {
+        nsub = a.nsub ? a.nsub[r] : 1;
+        if (nsub < 1 || nsub > RAM_MAX_NSUB) {
+            atomicOr(a.err, ERR_NSUB);
+            nsub = nsub < 1 ? 1 : RAM_MAX_NSUB;
+        }
+        P.cf = row.uniform ? (T)(a.dt * row.cells_per_length * inv_small(nsub))
+                           : (T)(a.dt * inv_small(nsub));
+    }
+    P.nsub = nsub;
+    return xi;
+}
+
 // Wait until the kernels this one depends on (programmatic dependent launch)
 // have finished and their writes are visible; a no-op for a normal launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

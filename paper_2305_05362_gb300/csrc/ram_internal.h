@@ -36,6 +36,20 @@ struct RowInfo {
     double inv_period;    // 1 / L
 };
 
+// Position of a row in the packed arrays, for kernels that stage whole rows.
+struct RowPos {
+    int64_t cell_off;
+    int32_t row;
+    int32_t n;
+};
+
+// A row of the streaming kernel's launch list: its table entry and its index.
+struct StreamRow {
+    RowInfo info;
+    int32_t row;
+    int32_t pad;
+};
+
 // One unit of work: output cells [start, start + count) of one row.
 struct Tile {
     int32_t row;
@@ -92,6 +106,7 @@ struct Plan {
     int32_t tile_cells = 1024;
     int32_t threads = 256;
     int32_t rows_v[2] = {7, 7};    // cells per thread of the whole-row kernel (FP32, FP64)
+    int32_t rows_cps[2] = {2, 1};  // CTAs per SM of the whole-row kernel (FP32, FP64)
     std::vector<int64_t> row_offset;
     std::vector<RowInfo> rows_h;
     std::vector<double> nodes_h;   // host copy of the FP64 nodes (per row or shared)
@@ -100,12 +115,19 @@ struct Plan {
     // uniform rows taken by the persistent whole-row kernel, per dtype and order, and
     // the tiles of the remaining uniform rows
     std::vector<int32_t> rows_fit_h[2][5];
+    std::vector<RowPos> rows_fit_pos_h[2][5];
     std::vector<Tile> tiles_rest_h[2][5];
     int32_t ncap_fit[2][5] = {{0}};
     // uniform rows taken by the warp-segment kernel, and the tiles of the others
     std::vector<int32_t> rows_seg_h[2][5];
     std::vector<Tile> tiles_rest_seg_h[2][5];
-    int32_t uniform_kernel[2] = {1, 1};  // 0: persistent whole-row, 1: warp segments
+    // FP32 rows of the streaming kernel (the warp-segment rows), by order
+    std::vector<StreamRow> stream_rows_h[5];
+    int32_t stream_nmax[5] = {0};
+    int32_t stream_nmin[5] = {0};
+    int32_t stream_v = 8;          // cells per lane of the streaming kernel
+    // 0: persistent whole-row, 1: warp segments, 2: streaming warps (FP32 only)
+    int32_t uniform_kernel[2] = {1, 1};
     int32_t n_uniform_rows = 0;
     int32_t window_max = 0;        // max planned source window (non-uniform tiles)
     // device
@@ -113,9 +135,11 @@ struct Plan {
     Tile *tiles_uniform[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     Tile *tiles_general[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t *rows_fit[2][5] = {{nullptr}};
+    RowPos *rows_fit_pos[2][5] = {{nullptr}};
     Tile *tiles_rest[2][5] = {{nullptr}};
     int32_t *rows_seg[2][5] = {{nullptr}};
     Tile *tiles_rest_seg[2][5] = {{nullptr}};
+    StreamRow *stream_rows[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     void *row_par = nullptr;        // RowParams<double> per row (FP32 launches use the first
                                     // half of each slot as RowParams<float>)
     uint64_t *xfix = nullptr;
@@ -156,9 +180,16 @@ cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const
                            void *g_in, void *g_dv, cudaStream_t s);
 
 cudaError_t launch_rows(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
-                        int order, const int32_t *row_ids, int n_rows, int ncap);
+                        int order, const RowPos *rows, int n_rows, int ncap);
 cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
                         int order, const int32_t *row_ids, int n_rows);
+
+// streaming kernel for the FP32 rows of one order in stream_rows (ram_stream.cu)
+cudaError_t launch_stream(const Plan &p, const StepArgs &a, cudaStream_t s, int order);
+// the smallest row the streaming kernel takes with v cells per lane
+int stream_min_cells(int v);
+extern const int kStreamVCandidates[];
+extern const int kStreamVCount;
 
 // tiling (ram_plan.cu)
 ram_status build_tiles(Plan &p);

@@ -76,8 +76,14 @@ void free_lists(Plan &p)
         p.tiles_uniform[o] = p.tiles_general[o] = nullptr;
         for (int d = 0; d < 2; ++d) {
             cudaFree(p.rows_fit[d][o]);
+            cudaFree(p.rows_fit_pos[d][o]);
+            p.rows_fit_pos[d][o] = nullptr;
             cudaFree(p.tiles_rest[d][o]);
             cudaFree(p.rows_seg[d][o]);
+            if (d == 0) {
+                cudaFree(p.stream_rows[o]);
+                p.stream_rows[o] = nullptr;
+            }
             cudaFree(p.tiles_rest_seg[d][o]);
             p.rows_fit[d][o] = nullptr;
             p.tiles_rest[d][o] = nullptr;
@@ -120,10 +126,16 @@ ram_status build_tiles(Plan &p)
         p.tiles_general_h[o].clear();
         for (int d = 0; d < 2; ++d) {
             p.rows_fit_h[d][o].clear();
+            p.rows_fit_pos_h[d][o].clear();
             p.tiles_rest_h[d][o].clear();
             p.ncap_fit[d][o] = 0;
             p.rows_seg_h[d][o].clear();
             p.tiles_rest_seg_h[d][o].clear();
+            if (d == 0) {
+                p.stream_rows_h[o].clear();
+                p.stream_nmax[o] = 0;
+                p.stream_nmin[o] = 0;
+            }
         }
     }
     p.window_max = 0;
@@ -148,6 +160,7 @@ ram_status build_tiles(Plan &p)
                     if (fit) {
                         if (t == 0) {
                             p.rows_fit_h[d][ri.order].push_back(r);
+                            p.rows_fit_pos_h[d][ri.order].push_back(RowPos{ri.cell_off, r, n});
                             int cap = (n + 15) / 16 * 16;
                             if (cap > p.ncap_fit[d][ri.order]) p.ncap_fit[d][ri.order] = cap;
                         }
@@ -158,7 +171,16 @@ ram_status build_tiles(Plan &p)
                     const bool seg = n >= 512 && (n * es) % 16 == 0 &&
                                      (ri.cell_off * es) % 16 == 0;
                     if (seg) {
-                        if (t == 0) p.rows_seg_h[d][ri.order].push_back(r);
+                        if (t == 0) {
+                            p.rows_seg_h[d][ri.order].push_back(r);
+                            if (d == 0) {
+                                p.stream_rows_h[ri.order].push_back(StreamRow{ri, r, 0});
+                                p.stream_nmax[ri.order] = std::max(p.stream_nmax[ri.order], n);
+                                p.stream_nmin[ri.order] = p.stream_nmin[ri.order] == 0
+                                                              ? n
+                                                              : std::min(p.stream_nmin[ri.order], n);
+                            }
+                        }
                     } else {
                         p.tiles_rest_seg_h[d][ri.order].push_back(tl);
                     }
@@ -217,6 +239,9 @@ ram_status build_tiles(Plan &p)
             if (upload(&p.rows_fit[d][o], p.rows_fit_h[d][o].data(),
                        p.rows_fit_h[d][o].size()) != cudaSuccess)
                 return RAM_ERR_NOMEM;
+            if (upload(&p.rows_fit_pos[d][o], p.rows_fit_pos_h[d][o].data(),
+                       p.rows_fit_pos_h[d][o].size()) != cudaSuccess)
+                return RAM_ERR_NOMEM;
             if (upload(&p.tiles_rest[d][o], p.tiles_rest_h[d][o].data(),
                        p.tiles_rest_h[d][o].size()) != cudaSuccess)
                 return RAM_ERR_NOMEM;
@@ -225,6 +250,9 @@ ram_status build_tiles(Plan &p)
                 return RAM_ERR_NOMEM;
             if (upload(&p.tiles_rest_seg[d][o], p.tiles_rest_seg_h[d][o].data(),
                        p.tiles_rest_seg_h[d][o].size()) != cudaSuccess)
+                return RAM_ERR_NOMEM;
+            if (d == 0 && upload(&p.stream_rows[o], p.stream_rows_h[o].data(),
+                                 p.stream_rows_h[o].size()) != cudaSuccess)
                 return RAM_ERR_NOMEM;
         }
     }

@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "ram_device.cuh"
+#include "ram_tma.cuh"
 
 namespace ram {
 namespace {
@@ -29,68 +30,10 @@ constexpr int kHaloS = 24;
 constexpr int kHaloP = 16;
 constexpr int kMaxStages = 3;
 constexpr int kMaxStagesH = 3;
-constexpr uint32_t kWaitLimit = 1u << 20;
 
 constexpr int kBatch = 32;  // rows whose parameters the producer warp computes at once
 // shared-memory header: barriers and the row parameters
 constexpr int kHeader = (6 * 8 + (kMaxStagesH + kBatch) * 80 + 127) / 128 * 128;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// 1D TMA bulk copy global -> shared, completing on an mbarrier.  Both addresses
-// 16-byte aligned, size a multiple of 16 (checked by the launcher).
-__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void consumer_sync(int nthreads)
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
 
 template <typename T>
 __device__ __forceinline__ T half_vl(T dl, T dr)
@@ -228,8 +171,9 @@ __device__ __forceinline__ void put_group(T *buf, int m0, int N, const T (&out)[
 }
 
 template <typename T, int ORDER, int V>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544, sizeof(T) == 4 ? 2 : 1)
-    k_rows(StepArgs a, const int32_t *row_ids, int n_rows, int ncap, int stages, int nwc,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
+                                  sizeof(T) == 4 ? (V <= 5 ? 4 : (V <= 9 ? 3 : 2)) : 1)
+    k_rows(StepArgs a, const RowPos *rpos, int n_rows, int ncap, int stages, int nwc,
            const RowParams<T> *pars)
 {
     static_assert(V + 3 <= kHaloS && V + 1 <= kHaloP, "halo too small for V");
@@ -281,10 +225,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544, sizeof(T) == 4 ? 2
             const int k = kb + lane;
             const int kend = min(kb + kBatch, my_rows);
             int r = -1;
-            RowInfo row;
+            RowPos row;
             if (k < my_rows) {
-                r = row_ids[blockIdx.x + k * gridDim.x];
-                row = a.rows[r];
+                row = rpos[blockIdx.x + k * gridDim.x];
+                r = row.row;
             }
             // lane j holds row kb+j's record; lane 0 issues copies for the rows of
             // this batch whose stage is free without waiting (the first `stages`)
@@ -420,32 +364,42 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544, sizeof(T) == 4 ? 2
 // thread (odd, a tuning parameter).
 template <typename T, int ORDER, int V>
 static cudaError_t launch_rows_v(const Plan &p, const StepArgs &a, cudaStream_t s,
-                                 const int32_t *row_ids, int n_rows, int ncap)
+                                 const RowPos *rows, int n_rows, int ncap)
 {
     const size_t es = sizeof(T);
     const size_t rowb = (size_t)(ncap + 2 * kHaloS) * es;
     const size_t pb = (size_t)(ncap + 2 * kHaloP) * es;
-    // FP32: two CTAs per SM (one CTA's barrier waits overlap the other's work);
-    // FP64: one
-    const int per_sm = sizeof(T) == 4 ? 2 : 1;
-    const size_t budget = (per_sm == 2 ? 110 : 220) * 1024;
-    int stages = kMaxStages;
-    while (stages > 1 && kHeader + 2 * stages * rowb + pb > budget) --stages;
-    size_t smem = kHeader + 2 * stages * rowb + pb;
-    if (smem > 220 * 1024) return cudaErrorNotSupported;
+    // CTAs per SM: the plan's choice, within what the register budget of this V
+    // allows; shared memory per CTA is the SM's share, filled with as many stages
+    // (up to three) as fit
+    const int cps_max = sizeof(T) == 4 ? (V <= 5 ? 4 : (V <= 9 ? 3 : 2)) : 1;
+    int cps = p.rows_cps[sizeof(T) == 4 ? 0 : 1];
+    if (cps > cps_max) cps = cps_max;
+    if (cps < 1) cps = 1;
+    int stages = 0;
+    size_t smem = 0;
+    for (; cps >= 1; --cps) {
+        const size_t budget = (size_t)(227 * 1024) / cps - 1024;
+        for (stages = kMaxStages; stages >= 1; --stages) {
+            smem = kHeader + 2 * stages * rowb + pb;
+            if (smem <= budget) break;
+        }
+        if (stages >= 1) break;
+    }
+    if (cps < 1 || stages < 1) return cudaErrorNotSupported;
     int groups = (ncap + V - 1) / V;
     const int nwc_max = sizeof(T) == 4 ? 8 : 16;  // within the launch bounds
     int nwc = (groups + 31) / 32;
     if (nwc > nwc_max) nwc = nwc_max;
     if (nwc < 4) nwc = 4;
-    static size_t configured[64] = {0};
+    static bool configured[64] = {false};
     const int dev = p.device < 64 ? p.device : 63;
-    if (smem > configured[dev]) {
+    if (!configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_rows<T, ORDER, V>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(220 * 1024));
+                                             (int)(227 * 1024));
         if (e != cudaSuccess) return e;
-        configured[dev] = 220 * 1024;
+        configured[dev] = true;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
@@ -453,22 +407,22 @@ static cudaError_t launch_rows_v(const Plan &p, const StepArgs &a, cudaStream_t 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_rows<T, ORDER, V>, 32 * (nwc + 1),
                                                   smem);
     if (fit < 1) fit = 1;
-    if (fit > per_sm) fit = per_sm;
+    if (fit > cps) fit = cps;
     const int grid = n_rows < sms * fit ? n_rows : sms * fit;
-    return launch_pdl(k_rows<T, ORDER, V>, grid, 32 * (nwc + 1), smem, s, a, row_ids, n_rows,
+    return launch_pdl(k_rows<T, ORDER, V>, grid, 32 * (nwc + 1), smem, s, a, rows, n_rows,
                       ncap, stages, nwc, static_cast<const RowParams<T> *>(p.row_par));
 }
 
 template <typename T, int ORDER>
 static cudaError_t launch_rows_t(const Plan &p, const StepArgs &a, cudaStream_t s,
-                                 const int32_t *row_ids, int n_rows, int ncap)
+                                 const RowPos *rows, int n_rows, int ncap)
 {
     switch (p.rows_v[sizeof(T) == 4 ? 0 : 1]) {
-    case 5: return launch_rows_v<T, ORDER, 5>(p, a, s, row_ids, n_rows, ncap);
-    case 9: return launch_rows_v<T, ORDER, 9>(p, a, s, row_ids, n_rows, ncap);
-    case 11: return launch_rows_v<T, ORDER, 11>(p, a, s, row_ids, n_rows, ncap);
-    case 15: return launch_rows_v<T, ORDER, 15>(p, a, s, row_ids, n_rows, ncap);
-    default: return launch_rows_v<T, ORDER, 7>(p, a, s, row_ids, n_rows, ncap);
+    case 5: return launch_rows_v<T, ORDER, 5>(p, a, s, rows, n_rows, ncap);
+    case 9: return launch_rows_v<T, ORDER, 9>(p, a, s, rows, n_rows, ncap);
+    case 11: return launch_rows_v<T, ORDER, 11>(p, a, s, rows, n_rows, ncap);
+    case 15: return launch_rows_v<T, ORDER, 15>(p, a, s, rows, n_rows, ncap);
+    default: return launch_rows_v<T, ORDER, 7>(p, a, s, rows, n_rows, ncap);
     }
 }
 
@@ -476,17 +430,17 @@ const int kRowsVCandidates[] = {5, 7, 9, 11, 15};
 const int kRowsVCount = 5;
 
 cudaError_t launch_rows(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
-                        int order, const int32_t *row_ids, int n_rows, int ncap)
+                        int order, const RowPos *rows, int n_rows, int ncap)
 {
     if (n_rows == 0) return cudaSuccess;
     if (dt == RAM_F32) {
-        if (order == 2) return launch_rows_t<float, 2>(p, a, s, row_ids, n_rows, ncap);
-        if (order == 3) return launch_rows_t<float, 3>(p, a, s, row_ids, n_rows, ncap);
-        return launch_rows_t<float, 4>(p, a, s, row_ids, n_rows, ncap);
+        if (order == 2) return launch_rows_t<float, 2>(p, a, s, rows, n_rows, ncap);
+        if (order == 3) return launch_rows_t<float, 3>(p, a, s, rows, n_rows, ncap);
+        return launch_rows_t<float, 4>(p, a, s, rows, n_rows, ncap);
     }
-    if (order == 2) return launch_rows_t<double, 2>(p, a, s, row_ids, n_rows, ncap);
-    if (order == 3) return launch_rows_t<double, 3>(p, a, s, row_ids, n_rows, ncap);
-    return launch_rows_t<double, 4>(p, a, s, row_ids, n_rows, ncap);
+    if (order == 2) return launch_rows_t<double, 2>(p, a, s, rows, n_rows, ncap);
+    if (order == 3) return launch_rows_t<double, 3>(p, a, s, rows, n_rows, ncap);
+    return launch_rows_t<double, 4>(p, a, s, rows, n_rows, ncap);
 }
 
 }  // namespace ram

@@ -1,0 +1,509 @@
+// Streaming RAM step for FP32 uniform rows: independent warps, each with its own
+// ring of shared-memory stages filled by asynchronous copies.
+//
+// Work unit: a pair of consecutive warp segments of one row, 64 x V consecutive
+// cells, lane l holding cells l V .. l V + V - 1 of the first segment (A) and the
+// same cells of the second (B) as the two halves of float2 registers, so that
+// the arithmetic runs on the packed FP32 pipe (two cells per instruction).  The
+// outermost H4 cells at each end of a pair are halo for the residual sub-steps
+// (a van Leer sub-step reaches two cells, a donor sub-step one; H4 rounds that
+// up to whole 16-byte vectors): consecutive pairs overlap by 2 H4 cells and each
+// stores only its interior.  Pair k of a row owns output cells [k U, k U + U),
+// U = 64 V - 2 H4.  Each warp takes a contiguous run of the pairs of all rows
+// (row-major), so a warp meets only one or two rows and computes their shift
+// parameters once (shift_params in FP64 on one lane per row: K whole cells and
+// the fraction's partial-integral coefficients, Sec. 3.2.1 on a uniform mesh).
+//
+// Per pair a lane rebuilds the PPM / PLM / order-4 partials of the V + 1 source
+// cells its cells need (App. A, Eq. 18), forms Q' = right part of p + left part
+// of p + 1 (Eq. 26) and runs the residual sub-steps (Eq. 6) in registers, with
+// the two-cell halos exchanged by warp shuffles (lane 31's A neighbours lane 0's
+// B).  The PPM limiters are written in the min/max-with-sign form (the ALU pipe
+// runs at half the FMA rate):
+//   2 dQ   = sign(D) min(|D|, 4 |dn|, 4 |up|) when dn up > 0, else 0   (App. A.2)
+//   a', b' = median(0, a, 2b), median(0, b, 2a)                         (App. A.2)
+// with D = Q_{i+1} - Q_{i-1}, a = QR - Q and b = Q - QL; the second line is the
+// flat / overshoot rule (a b <= 0: flat; |b| > 2|a|: QL = 3Q - 2QR; |a| > 2|b|:
+// QR = 3Q - 2QL).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ram_device.cuh"
+#include "ram_tma.cuh"
+
+namespace ram {
+
+const int kStreamVCandidates[] = {4, 8};
+const int kStreamVCount = 2;
+
+namespace {
+
+constexpr int kSWarps = 4;     // warps per CTA
+constexpr int kSStages = 3;    // stages per warp
+constexpr int kSHaloMax = 16;  // H4 for RAM_MAX_NSUB van Leer sub-steps
+constexpr int kRowBatch = 4;   // rows whose parameters a warp holds at once
+static_assert(kSHaloMax >= 2 * RAM_MAX_NSUB && kSHaloMax % 4 == 0, "halo bound");
+
+// Shift parameters of one row (the fields the pair kernel needs).
+struct RowRec {
+    int64_t cell_off;  // first cell of the row in the packed arrays
+    int32_t n;         // cells in the row
+    int32_t K;         // whole cells of the shift
+    int32_t nsub;      // residual sub-steps (0: none)
+    int32_t whole;     // the shift is a whole number of cells
+    int32_t delta;     // source window offset inside its first 16-byte vector
+    int32_t h4;        // halo cells at each end of a pair
+    float cf;          // Courant number per unit dv of one sub-step
+    float k[5];        // order 3: xi, c_R, -c_L; order 2: xi, slope; order 4: weights
+    int32_t pad[2];
+};
+static_assert(sizeof(RowRec) == 64, "row record layout");
+
+// One staged pair: the row's parameters and the pair's cells.
+struct PairRec {
+    RowRec row;
+    int32_t c0;      // first cell of the pair (may be negative: cyclic)
+    int32_t u0, u1;  // output cells [u0, u1) stored by this pair
+    int32_t pad;
+};
+static_assert(sizeof(PairRec) == 80, "pair record layout");
+
+template <int V>
+struct SLayout {
+    static constexpr int W = 64 * V;       // cells of a pair
+    static constexpr int Wq = W + 8;       // staged source cells
+    static constexpr int Wv = W + 4;       // staged dv nodes
+    static constexpr int stage_floats = Wq + Wv;
+    // per warp: [PairRec x S][RowRec x kRowBatch][stages]
+    static constexpr int rec_off = 0;
+    static constexpr int batch_off = rec_off + 80 * kSStages;
+    static constexpr int stage_off = batch_off + 64 * kRowBatch;
+    static constexpr int warp_bytes = stage_off + kSStages * stage_floats * 4;
+    static_assert(stage_off % 16 == 0 && (stage_floats * 4) % 16 == 0 && warp_bytes % 16 == 0,
+                  "16-byte aligned stages");
+};
+
+__device__ __forceinline__ float minxs(float a, float b)
+{
+    // min(|a|, |b|) carrying the sign sign(a) xor sign(b)
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+__device__ __forceinline__ float xorsign(float g, float a)
+{
+    // g with its sign flipped where a is negative
+    return __int_as_float(__float_as_int(g) ^ (__float_as_int(a) & 0x80000000));
+}
+
+__device__ __forceinline__ int mod_n(int x, int n)
+{
+    const int r = x % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Q' for the V output cells of one lane in both segments.  q[0..V+4] holds
+// source cells p0-2 .. p0+V+2 with p0 = m0 - K - 1, m0 the lane's first cell.
+template <int ORDER, int V>
+__device__ __forceinline__ void remap_pair(const float2 (&q)[V + 5], const RowRec &R, bool lim,
+                                           float2 (&out)[V])
+{
+    if (R.whole) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = q[k + 3];
+        return;
+    }
+    float2 A[V + 1];  // left partial integral of source cells p0 .. p0+V
+    if (ORDER == 3) {
+        float2 dif[V + 4];
+#pragma unroll
+        for (int i = 0; i < V + 4; ++i) dif[i] = sub2(q[i + 1], q[i]);
+        float2 Dq[V + 3];  // 2 dQ of source cells p0-1 .. p0+V+1
+#pragma unroll
+        for (int i = 0; i < V + 3; ++i) {
+            const float2 D = __fadd2_rn(dif[i], dif[i + 1]);
+            if (lim) {
+                float2 t = make_float2(minxs(dif[i].x, dif[i + 1].x), minxs(dif[i].y, dif[i + 1].y));
+                t = __fmul2_rn(t, f2(4.0f));
+                const float mx = fmaxf(fminf(fabsf(D.x), t.x), 0.0f);
+                const float my = fmaxf(fminf(fabsf(D.y), t.y), 0.0f);
+                Dq[i] = make_float2(minxs(D.x, mx), minxs(D.y, my));
+            } else {
+                Dq[i] = D;
+            }
+        }
+        float2 E[V + 2];  // 2 (dQ_{j+1} - dQ_j) for j = p0-1 .. p0+V
+#pragma unroll
+        for (int i = 0; i < V + 2; ++i) E[i] = sub2(Dq[i + 1], Dq[i]);
+        float2 h[V + 3];  // dif / 2 (index 1 .. V+2 used)
+#pragma unroll
+        for (int i = 1; i < V + 3; ++i) h[i] = __fmul2_rn(dif[i], f2(0.5f));
+        const float2 k0 = f2(R.k[0]), k1 = f2(R.k[1]), k2 = f2(R.k[2]);
+#pragma unroll
+        for (int j = 0; j <= V; ++j) {
+            // a = QR - Q = dif_j / 2 - E_j / 12,  b = Q - QL = dif_{j-1} / 2 + E_{j-1} / 12
+            const float2 a = __ffma2_rn(E[j + 1], f2(-1.0f / 12.0f), h[j + 2]);
+            const float2 b = __ffma2_rn(E[j], f2(1.0f / 12.0f), h[j + 1]);
+            float2 G;
+            if (lim) {
+                const float2 a2 = __ffma2_rn(E[j + 1], f2(-1.0f / 6.0f), dif[j + 2]);
+                const float2 b2 = __ffma2_rn(E[j], f2(1.0f / 6.0f), dif[j + 1]);
+                const float2 u = make_float2(fmaxf(minxs(a.x, b2.x), 0.0f),
+                                             fmaxf(minxs(a.y, b2.y), 0.0f));  // |a'|
+                const float2 v = make_float2(fmaxf(minxs(b.x, a2.x), 0.0f),
+                                             fmaxf(minxs(b.y, a2.y), 0.0f));  // |b'|
+                G = __ffma2_rn(k1, u, __fmul2_rn(k2, v));
+                G = make_float2(xorsign(G.x, a.x), xorsign(G.y, a.y));
+            } else {
+                G = __ffma2_rn(k1, a, __fmul2_rn(k2, b));
+            }
+            A[j] = __ffma2_rn(k0, q[j + 2], G);
+        }
+    } else if (ORDER == 2) {
+        const float2 k0 = f2(R.k[0]), k1 = f2(R.k[1]);
+#pragma unroll
+        for (int j = 0; j <= V; ++j) {
+            const float2 dn = sub2(q[j + 2], q[j + 1]), up = sub2(q[j + 3], q[j + 2]);
+            float2 sl;
+            if (lim) {
+                const float2 p = __fmul2_rn(dn, up);
+                const float2 s = __fadd2_rn(dn, up);
+                const float2 hh = __fmul2_rn(p, make_float2(__fdividef(2.0f, s.x),
+                                                            __fdividef(2.0f, s.y)));
+                sl = make_float2(p.x > 0.0f ? hh.x : 0.0f, p.y > 0.0f ? hh.y : 0.0f);
+            } else {
+                sl = __fmul2_rn(__fadd2_rn(dn, up), f2(0.5f));
+            }
+            A[j] = __ffma2_rn(q[j + 2], k0, __fmul2_rn(sl, k1));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j <= V; ++j) {
+            float2 s = __fmul2_rn(f2(R.k[0]), q[j]);
+#pragma unroll
+            for (int i = 1; i < 5; ++i) s = __ffma2_rn(f2(R.k[i]), q[j + i], s);
+            A[j] = s;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = __fadd2_rn(sub2(q[k + 2], A[k]), A[k + 1]);
+}
+
+// The residual sub-steps (Eq. 6) of one lane's cells in both segments.  v[0..V]
+// are the velocities at the lane's nodes m0..m0+V (node k is the left node of
+// cell m0+k).  The flux through node k is
+//   F = c+ (Q_{k-1} + h_{k-1} (1 - c+)) + c- (Q_k - h_k (1 + c-)),
+// c+ = max(c, 0), c- = min(c, 0), c = v cf, h the half van Leer slope (0 for
+// donor): the upwind value at the midpoint of the swept region.
+template <int V>
+__device__ __forceinline__ void residual_pair(float2 (&cur)[V], const float2 (&v)[V + 1], float cf,
+                                              int nsub, bool vl, int lane, float &cmax)
+{
+    float2 ap[V + 1], am[V + 1];
+#pragma unroll
+    for (int k = 0; k <= V; ++k) {
+        const float2 c = __fmul2_rn(v[k], f2(cf));
+        ap[k] = make_float2(fmaxf(c.x, 0.0f), fmaxf(c.y, 0.0f));
+        am[k] = sub2(c, ap[k]);
+        cmax = fmaxf(cmax, fmaxf(fabsf(c.x), fabsf(c.y)));
+    }
+    const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
+    for (int sub = 0; sub < nsub; ++sub) {
+        float2 z[V + 4];  // cells m0-2 .. m0+V+1
+        {
+            // lane 0's B continues lane 31's A; lane 31's A continues lane 0's B
+            const float l2x = __shfl_sync(0xffffffffu, cur[V - 2].x, up);
+            const float l2y = __shfl_sync(0xffffffffu, cur[V - 2].y, up);
+            const float l1x = __shfl_sync(0xffffffffu, cur[V - 1].x, up);
+            const float l1y = __shfl_sync(0xffffffffu, cur[V - 1].y, up);
+            const float r1x = __shfl_sync(0xffffffffu, cur[0].x, dn);
+            const float r1y = __shfl_sync(0xffffffffu, cur[0].y, dn);
+            const float r2x = __shfl_sync(0xffffffffu, cur[1].x, dn);
+            const float r2y = __shfl_sync(0xffffffffu, cur[1].y, dn);
+            z[0] = make_float2(l2x, lane == 0 ? l2x : l2y);
+            z[1] = make_float2(l1x, lane == 0 ? l1x : l1y);
+            z[V + 2] = make_float2(lane == 31 ? r1y : r1x, r1y);
+            z[V + 3] = make_float2(lane == 31 ? r2y : r2x, r2y);
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
+        float2 F[V + 1];
+        if (vl) {
+            float2 d[V + 3];
+#pragma unroll
+            for (int i = 0; i < V + 3; ++i) d[i] = sub2(z[i + 1], z[i]);
+            float2 h[V + 2];  // half slopes of cells m0-1 .. m0+V
+#pragma unroll
+            for (int c = 0; c < V + 2; ++c) {
+                const float2 p = __fmul2_rn(d[c], d[c + 1]);
+                const float2 s = __fadd2_rn(d[c], d[c + 1]);
+                const float2 hh =
+                    __fmul2_rn(p, make_float2(__fdividef(1.0f, s.x), __fdividef(1.0f, s.y)));
+                h[c] = make_float2(p.x > 0.0f ? hh.x : 0.0f, p.y > 0.0f ? hh.y : 0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k <= V; ++k) {
+                const float2 wp = __ffma2_rn(neg2(ap[k]), ap[k], ap[k]);          // c+ (1 - c+)
+                const float2 wm = __ffma2_rn(neg2(am[k]), am[k], neg2(am[k]));    // -c- (1 + c-)
+                float2 f = __fmul2_rn(am[k], z[k + 2]);
+                f = __ffma2_rn(ap[k], z[k + 1], f);
+                f = __ffma2_rn(wp, h[k], f);
+                F[k] = __ffma2_rn(wm, h[k + 1], f);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k <= V; ++k) F[k] = __ffma2_rn(ap[k], z[k + 1], __fmul2_rn(am[k], z[k + 2]));
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) cur[k] = sub2(z[k + 2], sub2(F[k + 1], F[k]));
+    }
+}
+
+// Shift parameters of list row ri (one lane per row).
+template <int V>
+__device__ __forceinline__ void row_rec(const StepArgs &a, const StreamRow *list, int ri, RowRec &R)
+{
+    const StreamRow e = list[ri];
+    RowParams<float> P;
+    const double xi = shift_params<float>(a, e.info, e.row, false, P);
+    const bool vl = a.scheme == RAM_VANLEER;
+    R.cell_off = P.cell_off;
+    R.n = P.n;
+    R.K = P.K;
+    R.nsub = P.nsub;
+    R.whole = P.whole;
+    R.delta = mod_n(-P.K - 3, 4);
+    R.h4 = ((P.nsub * (vl ? 2 : 1) + 3) / 4) * 4;
+    R.cf = P.cf;
+    if (e.info.order == 3) {
+        R.k[0] = (float)xi;
+        R.k[1] = P.c[1];
+        R.k[2] = -P.c[0];
+        R.k[3] = R.k[4] = 0.0f;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) R.k[j] = P.c[j];
+    }
+    R.pad[0] = R.pad[1] = 0;
+}
+
+template <int V>
+__device__ __forceinline__ void load_lane(const float *s, float (&w)[V + 8])
+{
+#pragma unroll
+    for (int c = 0; c < (V + 8) / 4; ++c) {
+        const float4 f4 = *reinterpret_cast<const float4 *>(s + 4 * c);
+        w[4 * c] = f4.x;
+        w[4 * c + 1] = f4.y;
+        w[4 * c + 2] = f4.z;
+        w[4 * c + 3] = f4.w;
+    }
+}
+
+template <int ORDER, int V>
+__global__ void __launch_bounds__(kSWarps * 32, V == 4 ? 6 : 4)
+    k_stream(StepArgs a, const StreamRow *list, int n_list, int pairs_per_row)
+{
+    static_assert(V % 4 == 0, "lanes start on 16-byte vectors");
+    using L = SLayout<V>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wb = smem_raw + (size_t)warp * L::warp_bytes;
+    PairRec *rec = reinterpret_cast<PairRec *>(wb + L::rec_off);
+    RowRec *batch = reinterpret_cast<RowRec *>(wb + L::batch_off);
+    float *stages = reinterpret_cast<float *>(wb + L::stage_off);
+
+    // this warp's contiguous run of pair slots (row-major over the list)
+    const long long G = (long long)gridDim.x * kSWarps;
+    const long long g = (long long)blockIdx.x * kSWarps + warp;
+    const long long total = (long long)n_list * pairs_per_row;
+    const int s_end = (int)((g + 1) * total / G);
+    int ip = (int)(g * total / G);  // next slot to look at
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    const bool vl = a.scheme == RAM_VANLEER;
+    const bool lim = a.limiter != 0;
+    const float *qin = static_cast<const float *>(a.q_in);
+    const float *dvin = static_cast<const float *>(a.dv);
+
+    int rb = -kRowBatch - 1;  // first list row of the parameter batch
+    int fp = 0;               // stages filled
+    auto issue_next = [&]() {
+        while (ip < s_end) {
+            const int sl = ip++;
+            const int ri = sl / pairs_per_row;
+            const int k = sl - ri * pairs_per_row;
+            if (ri < rb || ri >= rb + kRowBatch) {
+                rb = ri;
+                __syncwarp();
+                if (lane < kRowBatch && rb + lane < n_list) {
+                    RowRec R;
+                    row_rec<V>(a, list, rb + lane, R);
+                    batch[lane] = R;
+                }
+                __syncwarp();
+            }
+            const RowRec &R = batch[ri - rb];
+            const int n = R.n;
+            const int U = 64 * V - 2 * R.h4;
+            const int u0 = k * U;
+            if (u0 >= n) continue;  // past the end of this row
+            const int st = fp % kSStages;
+            const int c0 = u0 - R.h4;
+            if (lane == 0) {
+                rec[st].row = R;
+                rec[st].c0 = c0;
+                rec[st].u0 = u0;
+                rec[st].u1 = min(u0 + U, n);
+            }
+            float *sq = stages + (size_t)st * L::stage_floats;
+            // source window: the vector holding cell c0 - K - 3 onwards (cyclic)
+            const float *qrow = qin + R.cell_off;
+            const int qs = mod_n(c0 - R.K - 3 - R.delta, n);
+            for (int c = lane; c < L::Wq / 4; c += 32) {
+                int idx = qs + 4 * c;
+                if (idx >= n) idx -= n;
+                cp_async16(sq + 4 * c, qrow + idx);
+            }
+            if (has_dv && R.nsub > 0) {
+                const float *vrow = dvin + R.cell_off;
+                const int vs = mod_n(c0, n);
+                for (int c = lane; c < L::Wv / 4; c += 32) {
+                    int idx = vs + 4 * c;
+                    if (idx >= n) idx -= n;
+                    cp_async16(sq + L::Wq + 4 * c, vrow + idx);
+                }
+            }
+            cp_async_commit();
+            ++fp;
+            return;
+        }
+    };
+    for (int s = 0; s < kSStages; ++s) issue_next();
+
+    float cmax = 0.0f;
+    for (int fc = 0; fc < fp; ++fc) {
+        // this stage's copies are the oldest pending group of every lane
+        const int pend = fp - 1 - fc;
+        if (pend >= 2)
+            cp_async_wait<2>();
+        else if (pend == 1)
+            cp_async_wait<1>();
+        else
+            cp_async_wait<0>();
+        __syncwarp();
+        const int st = fc % kSStages;
+        const PairRec P = rec[st];
+        const float *sq = stages + (size_t)st * L::stage_floats;
+        float2 cur[V];
+        {
+            float wA[V + 8], wB[V + 8];
+            load_lane<V>(sq + lane * V, wA);
+            load_lane<V>(sq + 32 * V + lane * V, wB);
+            float2 q[V + 5];
+            switch (P.row.delta) {
+            case 0:
+#pragma unroll
+                for (int j = 0; j < V + 5; ++j) q[j] = make_float2(wA[j], wB[j]);
+                break;
+            case 1:
+#pragma unroll
+                for (int j = 0; j < V + 5; ++j) q[j] = make_float2(wA[j + 1], wB[j + 1]);
+                break;
+            case 2:
+#pragma unroll
+                for (int j = 0; j < V + 5; ++j) q[j] = make_float2(wA[j + 2], wB[j + 2]);
+                break;
+            default:
+#pragma unroll
+                for (int j = 0; j < V + 5; ++j) q[j] = make_float2(wA[j + 3], wB[j + 3]);
+                break;
+            }
+            remap_pair<ORDER, V>(q, P.row, lim, cur);
+        }
+        if (has_dv && P.row.nsub > 0) {
+            const float *sv = sq + L::Wq + lane * V;
+            float2 v[V + 1];
+#pragma unroll
+            for (int c = 0; c < V / 4; ++c) {
+                const float4 fa = *reinterpret_cast<const float4 *>(sv + 4 * c);
+                const float4 fb = *reinterpret_cast<const float4 *>(sv + 32 * V + 4 * c);
+                v[4 * c] = make_float2(fa.x, fb.x);
+                v[4 * c + 1] = make_float2(fa.y, fb.y);
+                v[4 * c + 2] = make_float2(fa.z, fb.z);
+                v[4 * c + 3] = make_float2(fa.w, fb.w);
+            }
+            v[V] = make_float2(sv[V], sv[32 * V + V]);
+            residual_pair<V>(cur, v, P.row.cf, P.row.nsub, vl, lane, cmax);
+        }
+        // store the interior vectors [u0, u1) of both segments
+        float *qo = static_cast<float *>(a.q_out) + P.row.cell_off;
+#pragma unroll
+        for (int c = 0; c < V / 4; ++c) {
+            const int ca = P.c0 + lane * V + 4 * c;
+            if (ca >= P.u0 && ca + 4 <= P.u1)
+                *reinterpret_cast<float4 *>(qo + ca) =
+                    make_float4(cur[4 * c].x, cur[4 * c + 1].x, cur[4 * c + 2].x, cur[4 * c + 3].x);
+            const int cb = ca + 32 * V;
+            if (cb >= P.u0 && cb + 4 <= P.u1)
+                *reinterpret_cast<float4 *>(qo + cb) =
+                    make_float4(cur[4 * c].y, cur[4 * c + 1].y, cur[4 * c + 2].y, cur[4 * c + 3].y);
+        }
+        // every lane has read the stage: it may be refilled
+        __syncwarp();
+        issue_next();
+    }
+    if (__any_sync(0xffffffffu, cmax > 1.0f) && lane == 0) atomicOr(a.err, ERR_CFL);
+    // the parameter kernel launched before this one may still be running; the
+    // launches after this one must see it finished
+    pdl_wait();
+}
+
+template <int ORDER, int V>
+cudaError_t launch_stream_v(const Plan &p, const StepArgs &a, cudaStream_t s)
+{
+    using L = SLayout<V>;
+    const int n_list = (int)p.stream_rows_h[ORDER].size();
+    if (n_list == 0) return cudaSuccess;
+    const int umin = 64 * V - 2 * kSHaloMax;
+    const int pairs_per_row = (p.stream_nmax[ORDER] + umin - 1) / umin;
+    const size_t smem = (size_t)kSWarps * L::warp_bytes;
+    static bool configured[64] = {false};
+    const int dev = p.device < 64 ? p.device : 63;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream<ORDER, V>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    int sms = 0, fit = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_stream<ORDER, V>, kSWarps * 32, smem);
+    if (fit < 1) fit = 1;
+    const long long total = (long long)n_list * pairs_per_row;
+    long long grid = (total + kSWarps - 1) / kSWarps;
+    if (grid > (long long)sms * fit) grid = (long long)sms * fit;
+    return launch_pdl(k_stream<ORDER, V>, (int)grid, kSWarps * 32, smem, s, a,
+                      static_cast<const StreamRow *>(p.stream_rows[ORDER]), n_list,
+                      pairs_per_row);
+}
+
+}  // namespace
+
+int stream_min_cells(int v) { return 64 * v + 8; }
+
+cudaError_t launch_stream(const Plan &p, const StepArgs &a, cudaStream_t s, int order)
+{
+    // a pair's staged window must not exceed its row (at most one cyclic wrap)
+    const bool v8 = p.stream_v == 8 && p.stream_nmin[order] >= stream_min_cells(8);
+    if (order == 2) return v8 ? launch_stream_v<2, 8>(p, a, s) : launch_stream_v<2, 4>(p, a, s);
+    if (order == 3) return v8 ? launch_stream_v<3, 8>(p, a, s) : launch_stream_v<3, 4>(p, a, s);
+    return v8 ? launch_stream_v<4, 8>(p, a, s) : launch_stream_v<4, 4>(p, a, s);
+}
+
+}  // namespace ram

@@ -41,6 +41,9 @@ extern "C" ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out)
     out->threads = p->threads;
     out->uniform_kernel_f32 = p->uniform_kernel[0];
     out->uniform_kernel_f64 = p->uniform_kernel[1];
+    out->rows_ctas_per_sm_f32 = p->rows_cps[0];
+    out->rows_ctas_per_sm_f64 = p->rows_cps[1];
+    out->stream_cells_per_lane_f32 = p->stream_v;
     return RAM_OK;
 }
 
@@ -49,8 +52,13 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     if (!plan || !t) return RAM_ERR_ARG;
     if (!valid_rows_v(t->rows_cells_per_thread_f32) || !valid_rows_v(t->rows_cells_per_thread_f64))
         return RAM_ERR_ARG;
-    if ((t->uniform_kernel_f32 != 0 && t->uniform_kernel_f32 != 1) ||
+    if (t->uniform_kernel_f32 < 0 || t->uniform_kernel_f32 > 2 ||
         (t->uniform_kernel_f64 != 0 && t->uniform_kernel_f64 != 1))
+        return RAM_ERR_ARG;
+    bool sv = false;
+    for (int i = 0; i < kStreamVCount; ++i) sv |= t->stream_cells_per_lane_f32 == kStreamVCandidates[i];
+    if (!sv) return RAM_ERR_ARG;
+    if (t->rows_ctas_per_sm_f32 < 1 || t->rows_ctas_per_sm_f32 > 4 || t->rows_ctas_per_sm_f64 != 1)
         return RAM_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (t->tile_cells != p->tile_cells || t->threads != p->threads) {
@@ -61,6 +69,9 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     p->rows_v[1] = t->rows_cells_per_thread_f64;
     p->uniform_kernel[0] = t->uniform_kernel_f32;
     p->uniform_kernel[1] = t->uniform_kernel_f64;
+    p->rows_cps[0] = t->rows_ctas_per_sm_f32;
+    p->rows_cps[1] = t->rows_ctas_per_sm_f64;
+    p->stream_v = t->stream_cells_per_lane_f32;
     return RAM_OK;
 }
 
@@ -104,7 +115,8 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
     for (int o = 2; o <= 4; ++o) any_seg |= !p->rows_seg_h[d][o].empty();
     if (any_rows || any_seg) {
         // candidates: (kernel, cells per thread)
-        int best_k = p->uniform_kernel[d], best_v = p->rows_v[d];
+        int best_k = p->uniform_kernel[d], best_v = p->rows_v[d], best_c = p->rows_cps[d];
+        int best_sv = p->stream_v;
         float best = 3.4e38f;
         if (any_seg) {
             p->uniform_kernel[d] = 1;
@@ -115,20 +127,40 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
                 best_k = 1;
             }
         }
-        if (any_rows)
-            for (int i = 0; i < kRowsVCount && st == RAM_OK; ++i) {
-                p->uniform_kernel[d] = 0;
-                p->rows_v[d] = kRowsVCandidates[i];
+        if (any_seg && d == 0)
+            for (int i = 0; i < kStreamVCount && st == RAM_OK; ++i) {
+                p->uniform_kernel[0] = 2;
+                p->stream_v = kStreamVCandidates[i];
                 float ms = 0;
                 st = time_once(&ms);
                 if (st == RAM_OK && ms < best) {
                     best = ms;
-                    best_k = 0;
-                    best_v = kRowsVCandidates[i];
+                    best_k = 2;
+                    best_sv = kStreamVCandidates[i];
+                }
+            }
+        if (any_rows)
+            for (int i = 0; i < kRowsVCount && st == RAM_OK; ++i) {
+                const int v = kRowsVCandidates[i];
+                const int cmax = d == 1 ? 1 : (v <= 5 ? 4 : (v <= 9 ? 3 : 2));
+                for (int c = (d == 1 ? 1 : 2); c <= cmax && st == RAM_OK; ++c) {
+                    p->uniform_kernel[d] = 0;
+                    p->rows_v[d] = v;
+                    p->rows_cps[d] = c;
+                    float ms = 0;
+                    st = time_once(&ms);
+                    if (st == RAM_OK && ms < best) {
+                        best = ms;
+                        best_k = 0;
+                        best_v = v;
+                        best_c = c;
+                    }
                 }
             }
         p->uniform_kernel[d] = best_k;
         p->rows_v[d] = best_v;
+        p->rows_cps[d] = best_c;
+        p->stream_v = best_sv;
     }
     if (any_tiles && st == RAM_OK) {
         const int tcs[] = {256, 512, 1024, 2048};

@@ -190,6 +190,14 @@ cudaError_t launch_order(const Plan &p, const StepArgs &a, cudaStream_t s)
     const bool vec_ok = aligned16(a.q_in) && aligned16(a.dv) && aligned16(a.q_out);
     if (!vec_ok)
         return launch_tiles<T, ORDER>(p, a, s, p.tiles_uniform[ORDER], p.tiles_uniform_h[ORDER]);
+    if (d == 0 && p.uniform_kernel[0] == 2 && !p.stream_rows_h[ORDER].empty()) {
+        // streaming warps: the same rows as the warp-segment kernel (16-byte aligned,
+        // at least 512 cells: no shorter than the staged window of 4 cells per lane)
+        cudaError_t e = launch_stream(p, a, s, ORDER);
+        if (e != cudaSuccess) return e;
+        return launch_tiles<T, ORDER>(p, a, s, p.tiles_rest_seg[d][ORDER],
+                                      p.tiles_rest_seg_h[d][ORDER]);
+    }
     if (p.uniform_kernel[d] == 1 && !p.rows_seg_h[d][ORDER].empty()) {
         cudaError_t e = launch_useg(p, dt, a, s, ORDER, p.rows_seg[d][ORDER],
                                     (int)p.rows_seg_h[d][ORDER].size());
@@ -199,7 +207,7 @@ cudaError_t launch_order(const Plan &p, const StepArgs &a, cudaStream_t s)
     }
     if (p.rows_fit_h[d][ORDER].empty())
         return launch_tiles<T, ORDER>(p, a, s, p.tiles_uniform[ORDER], p.tiles_uniform_h[ORDER]);
-    cudaError_t e = launch_rows(p, dt, a, s, ORDER, p.rows_fit[d][ORDER],
+    cudaError_t e = launch_rows(p, dt, a, s, ORDER, p.rows_fit_pos[d][ORDER],
                                 (int)p.rows_fit_h[d][ORDER].size(), p.ncap_fit[d][ORDER]);
     if (e != cudaSuccess) return e;
     return launch_tiles<T, ORDER>(p, a, s, p.tiles_rest[d][ORDER], p.tiles_rest_h[d][ORDER]);

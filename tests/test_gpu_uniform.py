@@ -315,7 +315,7 @@ def test_autotune_and_tuning_roundtrip():
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
 @pytest.mark.parametrize("scheme,nsub_max", [(ram.VANLEER, 8), (ram.DONOR, 8), (ram.VANLEER, 1)])
 def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
-    """The warp-segment kernel and the persistent whole-row kernel against the
+    """The warp-segment, persistent whole-row and streaming-warp kernels against the
     oracle, with sub-step counts up to the maximum (widest warp halos) and rows
     long enough for several warp segments."""
     n_r, n_phi = 6, 2048
@@ -336,10 +336,14 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
                                        oracle.shift_from_velocity(v0[r], dt), 3, True,
                                        dvr[r * n_phi:(r + 1) * n_phi], dt, scheme, int(nsub[r]))
                            for r in range(n_r)])
-    for kern in (0, 1):
+    # kernels: 0 whole-row, 1 warp segments, 2 streaming warps (FP32; V = 4, 8)
+    for kern, sv in ((0, 8), (1, 8), (2, 4), (2, 8)):
+        if kern == 2 and dtype == "float64":
+            continue
         t = plan.tuning()
         t.uniform_kernel_f32 = kern
-        t.uniform_kernel_f64 = kern
+        t.uniform_kernel_f64 = min(kern, 1)
+        t.stream_cells_per_lane_f32 = sv
         plan.set_tuning(t)
         out = torch.empty_like(qd)
         ram.step(plan, qd, out, _t(v0, torch.float64), dt, dv=dvd, scheme=scheme,
@@ -349,5 +353,5 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
         for r in range(n_r):
             sl = slice(r * n_phi, (r + 1) * n_phi)
             err = np.sum(np.abs(got[sl] - refs[sl])) / np.sum(np.abs(refs[sl]))
-            assert err <= TOL[dtype], (kern, r, err)
+            assert err <= TOL[dtype], (kern, sv, r, err)
     assert plan.check_errors() == 0
