@@ -50,8 +50,7 @@ def _workload(name, rank):
     if name == "disk":
         return wl.disk(n_r=1024, n_phi=4096, seed_dv=4 + rank, dtype=np.float32)
     if name == "disk_large":
-        return wl.disk(n_r=8192, n_phi=16384, seed_dv=4 + rank, ref_n_phi=4096,
-                       dtype=np.float32)
+        return wl.disk(n_r=8192, n_phi=16384, seed_dv=4 + rank, dtype=np.float32)
     if name == "batched":
         return wl.batched(n_rows=512, seed_len=6 + 100 * rank)
     raise SystemExit("unknown workload %s" % name)

@@ -18,6 +18,33 @@ template <> struct Num<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
 };
 
+// min(|a|, |b|) carrying the sign sign(a) xor sign(b): positive when a and b have
+// the same sign.  With it the limiters of App. A.2 need no compare-and-select:
+// median(0, x, y) = sign(x) max(minxs(x, y), 0).
+__device__ __forceinline__ float minxs(float a, float b)
+{
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ double minxs(double a, double b)
+{
+    const double m = fmin(fabs(a), fabs(b));
+    return __longlong_as_double(__double_as_longlong(m) |
+                                ((__double_as_longlong(a) ^ __double_as_longlong(b)) &
+                                 (long long)0x8000000000000000ull));
+}
+// g with its sign flipped where a is negative
+__device__ __forceinline__ float xorsign(float g, float a)
+{
+    return __int_as_float(__float_as_int(g) ^ (__float_as_int(a) & 0x80000000));
+}
+__device__ __forceinline__ double xorsign(double g, double a)
+{
+    return __longlong_as_double(__double_as_longlong(g) ^
+                                (__double_as_longlong(a) & (long long)0x8000000000000000ull));
+}
+
 // Reduce x to [0, p) with a floor-mod in FP64 (the shift may be any real).
 __device__ __forceinline__ double reduce_mod(double x, double p)
 {
@@ -127,19 +154,20 @@ __device__ __forceinline__ void ppm_u(T qm2, T qm1, T q0, T qp1, T qp2, bool lim
 // {-2,-1,0,1,2} and {-1,0,1,2,3} (in cells, relative to the cell's left node),
 // folded into five coefficients c[k] of Q_{i-2+k} so that G/dx = sum c[k] Q.
 // The Lagrange denominators of five equally spaced nodes are 24, -6, 4, -6, 24.
-__device__ __forceinline__ void quartic_coeffs_u(double xi, double c[5])
+template <typename U>
+__device__ __forceinline__ void quartic_coeffs_u(U xi, U c[5])
 {
-    const double inv_den[5] = {1.0 / 24.0, -1.0 / 6.0, 0.25, -1.0 / 6.0, 1.0 / 24.0};
-    double w[6] = {0, 0, 0, 0, 0, 0};
+    const U inv_den[5] = {U(1) / U(24), U(-1) / U(6), U(0.25), U(-1) / U(6), U(1) / U(24)};
+    U w[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            double l = inv_den[k];
+            U l = inv_den[k];
 #pragma unroll
             for (int j = 0; j < 5; ++j)
-                if (j != k) l *= xi - (double)(side + j - 2);
-            w[side + k] += 0.5 * l;
+                if (j != k) l *= xi - (U)(side + j - 2);
+            w[side + k] += U(0.5) * l;
         }
     }
     // node values relative to the cell's left node, in units of dx:
@@ -151,17 +179,40 @@ __device__ __forceinline__ void quartic_coeffs_u(double xi, double c[5])
     c[4] = w[5];
 }
 
+// Coefficients of the left partial integral G/dx at the edge offset xi for the
+// row's order (computed in U, stored in T):
+//   PLM  G/dx = Q xi + slope (xi^2 - xi)/2                      c = {xi, (xi^2 - xi)/2}
+//   PPM  G/dx = QL (xi - xi^2/2) + QR xi^2/2 + Q6 (xi^2/2 - xi^3/3), folded with
+//        Q6 = 6Q - 3(QL + QR) into coefficients of QL, QR and Q (c[0..2]; c[3] = xi,
+//        the coefficient of Q once QL, QR are written as Q - b, Q + a)
+//   order 4: Lagrange weights of the two quartics of the cumulative mass.
+template <typename U, typename T>
+__device__ __forceinline__ void partial_coeffs(int order, U xi, T (&c)[5])
+{
+    for (int j = 0; j < 5; ++j) c[j] = T(0);
+    if (order == 2) {
+        c[0] = (T)xi;
+        c[1] = (T)(U(0.5) * (xi * xi - xi));
+    } else if (order == 3) {
+        const U c0 = xi - U(0.5) * xi * xi, c1 = U(0.5) * xi * xi;
+        const U c6 = U(0.5) * xi * xi - xi * xi * xi * (U(1) / U(3));
+        c[0] = (T)(c0 - U(3) * c6);
+        c[1] = (T)(c1 - U(3) * c6);
+        c[2] = (T)(U(6) * c6);
+        c[3] = (T)xi;
+    } else {
+        U w[5];
+        quartic_coeffs_u(xi, w);
+        for (int j = 0; j < 5; ++j) c[j] = (T)w[j];
+    }
+}
+
 // The shift parameters of one row for one launch (S0), in FP64: the bulk
 // displacement s (row_shift), the accumulated phase (advanced by s when
 // update_phase), the fixed-point shift of rows with their own mesh, and for
 // uniform rows sig = (s mod L) N / L split into K = floor(sig) whole cells and
 // the fraction f, with the coefficients of the left partial integral at the
-// edge offset xi = 1 - f:
-//   PLM  G/dx = Q xi + slope (xi^2 - xi)/2,
-//   PPM  G/dx = QL (xi - xi^2/2) + QR xi^2/2 + Q6 (xi^2/2 - xi^3/3), folded with
-//        Q6 = 6Q - 3(QL + QR) into coefficients of QL, QR and Q,
-//   order 4: Lagrange weights of the two quartics of the cumulative mass;
-// and cf = dt / (nsub dx), the Courant number per unit dv of one residual
+// edge offset xi = 1 - f (partial_coeffs); and cf = dt / (nsub dx), the Courant number per unit dv of one residual
 // sub-step.  Returns xi.  Every kernel that needs these values computes them
 // with this function, so they agree bit for bit.
 template <typename T>
@@ -177,8 +228,9 @@ __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo 
     const double sred = reduce_mod_rcp(sft, row.period, row.inv_period);
     // fixed-point shift for rows with their own mesh: nodes are stored as fractions
     // of the period in units of 2^-64, so x - s and the periodic wrap are exact
-    // integer arithmetic
-    {
+    // integer arithmetic (uniform rows locate their edges by index instead)
+    P.sfix = 0ull;
+    if (!row.uniform) {
         const double t = sred * row.inv_period;  // in [0, 1]
         P.sfix = (t >= 1.0) ? 0ull : __double2ull_rn(t * 18446744073709551616.0);
     }
@@ -189,21 +241,13 @@ __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo 
     P.K = (int)Kd;
     P.whole = (f == 0.0);
     const double xi = 1.0 - f;
-    for (int j = 0; j < 5; ++j) P.c[j] = T(0);
-    if (row.order == 2) {
-        P.c[0] = (T)xi;
-        P.c[1] = (T)(0.5 * (xi * xi - xi));
-    } else if (row.order == 3) {
-        const double c0 = xi - 0.5 * xi * xi, c1 = 0.5 * xi * xi;
-        const double c6 = 0.5 * xi * xi - xi * xi * xi * (1.0 / 3.0);
-        P.c[0] = (T)(c0 - 3.0 * c6);
-        P.c[1] = (T)(c1 - 3.0 * c6);
-        P.c[2] = (T)(6.0 * c6);
-    } else {
-        double c[5];
-        quartic_coeffs_u(xi, c);
-        for (int j = 0; j < 5; ++j) P.c[j] = (T)c[j];
-    }
+    // the coefficients in the precision of the cells: FP64 work per row is what
+    // decides K and f (an FP64 instruction costs a warp tens of cycles on this
+    // part, so FP32 rows keep it to the few operations above)
+    if (sizeof(T) == 4)
+        partial_coeffs<float>(row.order, (float)xi, P.c);
+    else
+        partial_coeffs<double>(row.order, xi, P.c);
     const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
     int nsub = 0;
     P.cf = T(0);
@@ -213,8 +257,11 @@ __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo 
             atomicOr(a.err, ERR_NSUB);
             nsub = nsub < 1 ? 1 : RAM_MAX_NSUB;
         }
-        P.cf = row.uniform ? (T)(a.dt * row.cells_per_length * inv_small(nsub))
-                           : (T)(a.dt * inv_small(nsub));
+        if (sizeof(T) == 4)
+            P.cf = (T)(row.uniform ? a.dt * row.cells_per_length : a.dt) / (T)nsub;
+        else
+            P.cf = row.uniform ? (T)(a.dt * row.cells_per_length * inv_small(nsub))
+                               : (T)(a.dt * inv_small(nsub));
     }
     P.nsub = nsub;
     return xi;

@@ -43,13 +43,6 @@ struct RowPos {
     int32_t n;
 };
 
-// A row of the streaming kernel's launch list: its table entry and its index.
-struct StreamRow {
-    RowInfo info;
-    int32_t row;
-    int32_t pad;
-};
-
 // One unit of work: output cells [start, start + count) of one row.
 struct Tile {
     int32_t row;
@@ -121,8 +114,8 @@ struct Plan {
     // uniform rows taken by the warp-segment kernel, and the tiles of the others
     std::vector<int32_t> rows_seg_h[2][5];
     std::vector<Tile> tiles_rest_seg_h[2][5];
-    // FP32 rows of the streaming kernel (the warp-segment rows), by order
-    std::vector<StreamRow> stream_rows_h[5];
+    // longest and shortest FP32 warp-segment row, by order (the streaming kernel
+    // takes the same rows)
     int32_t stream_nmax[5] = {0};
     int32_t stream_nmin[5] = {0};
     int32_t stream_v = 8;          // cells per lane of the streaming kernel
@@ -139,7 +132,6 @@ struct Plan {
     Tile *tiles_rest[2][5] = {{nullptr}};
     int32_t *rows_seg[2][5] = {{nullptr}};
     Tile *tiles_rest_seg[2][5] = {{nullptr}};
-    StreamRow *stream_rows[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     void *row_par = nullptr;        // RowParams<double> per row (FP32 launches use the first
                                     // half of each slot as RowParams<float>)
     uint64_t *xfix = nullptr;
@@ -184,7 +176,7 @@ cudaError_t launch_rows(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStre
 cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
                         int order, const int32_t *row_ids, int n_rows);
 
-// streaming kernel for the FP32 rows of one order in stream_rows (ram_stream.cu)
+// streaming kernel for the FP32 warp-segment rows of one order (ram_stream.cu)
 cudaError_t launch_stream(const Plan &p, const StepArgs &a, cudaStream_t s, int order);
 // the smallest row the streaming kernel takes with v cells per lane
 int stream_min_cells(int v);

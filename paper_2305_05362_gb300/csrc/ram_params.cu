@@ -10,7 +10,7 @@ namespace ram {
 namespace {
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_params(StepArgs a, int n_rows, RowParams<T> *out)
+__global__ void __launch_bounds__(32) k_params(StepArgs a, int n_rows, RowParams<T> *out)
 {
     // the row kernels that follow may start now; they wait for these results
     pdl_trigger();
@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(128) k_params(StepArgs a, int n_rows, RowParam
 
 cudaError_t launch_params(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s)
 {
-    const int threads = 128;
+    // one warp per CTA: the FP64 work of the rows spreads over many SMs
+    const int threads = 32;
     const int blocks = (p.n_rows + threads - 1) / threads;
     if (dt == RAM_F32)
         k_params<float><<<blocks, threads, 0, s>>>(a, p.n_rows,

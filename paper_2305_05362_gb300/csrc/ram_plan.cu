@@ -80,10 +80,6 @@ void free_lists(Plan &p)
             p.rows_fit_pos[d][o] = nullptr;
             cudaFree(p.tiles_rest[d][o]);
             cudaFree(p.rows_seg[d][o]);
-            if (d == 0) {
-                cudaFree(p.stream_rows[o]);
-                p.stream_rows[o] = nullptr;
-            }
             cudaFree(p.tiles_rest_seg[d][o]);
             p.rows_fit[d][o] = nullptr;
             p.tiles_rest[d][o] = nullptr;
@@ -132,7 +128,6 @@ ram_status build_tiles(Plan &p)
             p.rows_seg_h[d][o].clear();
             p.tiles_rest_seg_h[d][o].clear();
             if (d == 0) {
-                p.stream_rows_h[o].clear();
                 p.stream_nmax[o] = 0;
                 p.stream_nmin[o] = 0;
             }
@@ -174,7 +169,6 @@ ram_status build_tiles(Plan &p)
                         if (t == 0) {
                             p.rows_seg_h[d][ri.order].push_back(r);
                             if (d == 0) {
-                                p.stream_rows_h[ri.order].push_back(StreamRow{ri, r, 0});
                                 p.stream_nmax[ri.order] = std::max(p.stream_nmax[ri.order], n);
                                 p.stream_nmin[ri.order] = p.stream_nmin[ri.order] == 0
                                                               ? n
@@ -250,9 +244,6 @@ ram_status build_tiles(Plan &p)
                 return RAM_ERR_NOMEM;
             if (upload(&p.tiles_rest_seg[d][o], p.tiles_rest_seg_h[d][o].data(),
                        p.tiles_rest_seg_h[d][o].size()) != cudaSuccess)
-                return RAM_ERR_NOMEM;
-            if (d == 0 && upload(&p.stream_rows[o], p.stream_rows_h[o].data(),
-                                 p.stream_rows_h[o].size()) != cudaSuccess)
                 return RAM_ERR_NOMEM;
         }
     }

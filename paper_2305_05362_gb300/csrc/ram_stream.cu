@@ -10,9 +10,9 @@
 // up to whole 16-byte vectors): consecutive pairs overlap by 2 H4 cells and each
 // stores only its interior.  Pair k of a row owns output cells [k U, k U + U),
 // U = 64 V - 2 H4.  Each warp takes a contiguous run of the pairs of all rows
-// (row-major), so a warp meets only one or two rows and computes their shift
-// parameters once (shift_params in FP64 on one lane per row: K whole cells and
-// the fraction's partial-integral coefficients, Sec. 3.2.1 on a uniform mesh).
+// (row-major), so a warp meets only one or two rows; their shift parameters (K
+// whole cells and the fraction's partial-integral coefficients, Sec. 3.2.1 on a
+// uniform mesh) come from the parameter kernel launched just before.
 //
 // Per pair a lane rebuilds the PPM / PLM / order-4 partials of the V + 1 source
 // cells its cells need (App. A, Eq. 18), forms Q' = right part of p + left part
@@ -42,7 +42,6 @@ namespace {
 constexpr int kSWarps = 4;     // warps per CTA
 constexpr int kSStages = 3;    // stages per warp
 constexpr int kSHaloMax = 16;  // H4 for RAM_MAX_NSUB van Leer sub-steps
-constexpr int kRowBatch = 4;   // rows whose parameters a warp holds at once
 static_assert(kSHaloMax >= 2 * RAM_MAX_NSUB && kSHaloMax % 4 == 0, "halo bound");
 
 // Shift parameters of one row (the fields the pair kernel needs).
@@ -75,38 +74,17 @@ struct SLayout {
     static constexpr int Wq = W + 8;       // staged source cells
     static constexpr int Wv = W + 4;       // staged dv nodes
     static constexpr int stage_floats = Wq + Wv;
-    // per warp: [PairRec x S][RowRec x kRowBatch][stages]
+    // per warp: [PairRec x S][RowRec of the producer's row][stages]
     static constexpr int rec_off = 0;
-    static constexpr int batch_off = rec_off + 80 * kSStages;
-    static constexpr int stage_off = batch_off + 64 * kRowBatch;
+    static constexpr int row_off = rec_off + 80 * kSStages;
+    static constexpr int stage_off = row_off + 64;
     static constexpr int warp_bytes = stage_off + kSStages * stage_floats * 4;
     static_assert(stage_off % 16 == 0 && (stage_floats * 4) % 16 == 0 && warp_bytes % 16 == 0,
                   "16-byte aligned stages");
 };
 
-__device__ __forceinline__ float minxs(float a, float b)
-{
-    // min(|a|, |b|) carrying the sign sign(a) xor sign(b)
-    float d;
-    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
-    return d;
-}
-
-__device__ __forceinline__ float xorsign(float g, float a)
-{
-    // g with its sign flipped where a is negative
-    return __int_as_float(__float_as_int(g) ^ (__float_as_int(a) & 0x80000000));
-}
-
-__device__ __forceinline__ int mod_n(int x, int n)
-{
-    const int r = x % n;
-    return r < 0 ? r + n : r;
-}
-
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // Q' for the V output cells of one lane in both segments.  q[0..V+4] holds
 // source cells p0-2 .. p0+V+2 with p0 = m0 - K - 1, m0 the lane's first cell.
@@ -249,8 +227,9 @@ __device__ __forceinline__ void residual_pair(float2 (&cur)[V], const float2 (&v
             }
 #pragma unroll
             for (int k = 0; k <= V; ++k) {
-                const float2 wp = __ffma2_rn(neg2(ap[k]), ap[k], ap[k]);          // c+ (1 - c+)
-                const float2 wm = __ffma2_rn(neg2(am[k]), am[k], neg2(am[k]));    // -c- (1 + c-)
+                // c+ (1 - c+) and -c- (1 + c-) = c- (-1 - c-)
+                const float2 wp = __fmul2_rn(ap[k], __ffma2_rn(ap[k], f2(-1.0f), f2(1.0f)));
+                const float2 wm = __fmul2_rn(am[k], __ffma2_rn(am[k], f2(-1.0f), f2(-1.0f)));
                 float2 f = __fmul2_rn(am[k], z[k + 2]);
                 f = __ffma2_rn(ap[k], z[k + 1], f);
                 f = __ffma2_rn(wp, h[k], f);
@@ -265,24 +244,20 @@ __device__ __forceinline__ void residual_pair(float2 (&cur)[V], const float2 (&v
     }
 }
 
-// Shift parameters of list row ri (one lane per row).
-template <int V>
-__device__ __forceinline__ void row_rec(const StepArgs &a, const StreamRow *list, int ri, RowRec &R)
+// The row's parameters as the pair kernel uses them, from the parameter kernel's
+// record.
+__device__ __forceinline__ void row_rec(const RowParams<float> &P, int order, bool vl, RowRec &R)
 {
-    const StreamRow e = list[ri];
-    RowParams<float> P;
-    const double xi = shift_params<float>(a, e.info, e.row, false, P);
-    const bool vl = a.scheme == RAM_VANLEER;
     R.cell_off = P.cell_off;
     R.n = P.n;
     R.K = P.K;
     R.nsub = P.nsub;
     R.whole = P.whole;
-    R.delta = mod_n(-P.K - 3, 4);
+    R.delta = (-P.K - 3) & 3;
     R.h4 = ((P.nsub * (vl ? 2 : 1) + 3) / 4) * 4;
     R.cf = P.cf;
-    if (e.info.order == 3) {
-        R.k[0] = (float)xi;
+    if (order == 3) {
+        R.k[0] = P.c[3];
         R.k[1] = P.c[1];
         R.k[2] = -P.c[0];
         R.k[3] = R.k[4] = 0.0f;
@@ -308,7 +283,8 @@ __device__ __forceinline__ void load_lane(const float *s, float (&w)[V + 8])
 
 template <int ORDER, int V>
 __global__ void __launch_bounds__(kSWarps * 32, V == 4 ? 6 : 4)
-    k_stream(StepArgs a, const StreamRow *list, int n_list, int pairs_per_row)
+    k_stream(StepArgs a, const int32_t *rows, int n_list, int pairs_per_row,
+             const RowParams<float> *pars)
 {
     static_assert(V % 4 == 0, "lanes start on 16-byte vectors");
     using L = SLayout<V>;
@@ -316,42 +292,51 @@ __global__ void __launch_bounds__(kSWarps * 32, V == 4 ? 6 : 4)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = smem_raw + (size_t)warp * L::warp_bytes;
     PairRec *rec = reinterpret_cast<PairRec *>(wb + L::rec_off);
-    RowRec *batch = reinterpret_cast<RowRec *>(wb + L::batch_off);
+    RowRec *prow = reinterpret_cast<RowRec *>(wb + L::row_off);
     float *stages = reinterpret_cast<float *>(wb + L::stage_off);
 
     // this warp's contiguous run of pair slots (row-major over the list)
     const long long G = (long long)gridDim.x * kSWarps;
     const long long g = (long long)blockIdx.x * kSWarps + warp;
     const long long total = (long long)n_list * pairs_per_row;
+    const int s_begin = (int)(g * total / G);
     const int s_end = (int)((g + 1) * total / G);
-    int ip = (int)(g * total / G);  // next slot to look at
     const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
     const bool vl = a.scheme == RAM_VANLEER;
     const bool lim = a.limiter != 0;
     const float *qin = static_cast<const float *>(a.q_in);
     const float *dvin = static_cast<const float *>(a.dv);
 
-    int rb = -kRowBatch - 1;  // first list row of the parameter batch
-    int fp = 0;               // stages filled
+    // the shift parameters come from the parameter kernel launched just before
+    pdl_wait();
+
+    // producer cursor: slot, its row (list index) and pair index in the row
+    int ip = s_begin;
+    int ri = s_begin / pairs_per_row, k = s_begin - ri * pairs_per_row;
+    int rcur = -1;  // list index whose parameters prow holds
+    int fp = 0;     // stages filled
     auto issue_next = [&]() {
         while (ip < s_end) {
-            const int sl = ip++;
-            const int ri = sl / pairs_per_row;
-            const int k = sl - ri * pairs_per_row;
-            if (ri < rb || ri >= rb + kRowBatch) {
-                rb = ri;
+            if (ri != rcur) {
                 __syncwarp();
-                if (lane < kRowBatch && rb + lane < n_list) {
-                    RowRec R;
-                    row_rec<V>(a, list, rb + lane, R);
-                    batch[lane] = R;
+                if (lane == 0) {
+                    RowRec t;
+                    row_rec(pars[rows[ri]], ORDER, vl, t);
+                    *prow = t;
                 }
                 __syncwarp();
+                rcur = ri;
             }
-            const RowRec &R = batch[ri - rb];
+            const RowRec &R = *prow;
+            const int kk = k;
+            ++ip;
+            if (++k == pairs_per_row) {
+                k = 0;
+                ++ri;
+            }
             const int n = R.n;
             const int U = 64 * V - 2 * R.h4;
-            const int u0 = k * U;
+            const int u0 = kk * U;
             if (u0 >= n) continue;  // past the end of this row
             const int st = fp % kSStages;
             const int c0 = u0 - R.h4;
@@ -364,7 +349,9 @@ __global__ void __launch_bounds__(kSWarps * 32, V == 4 ? 6 : 4)
             float *sq = stages + (size_t)st * L::stage_floats;
             // source window: the vector holding cell c0 - K - 3 onwards (cyclic)
             const float *qrow = qin + R.cell_off;
-            const int qs = mod_n(c0 - R.K - 3 - R.delta, n);
+            int qs = c0 - R.K - 3 - R.delta;
+            if (qs < 0) qs += n;
+            if (qs < 0) qs += n;
             for (int c = lane; c < L::Wq / 4; c += 32) {
                 int idx = qs + 4 * c;
                 if (idx >= n) idx -= n;
@@ -372,7 +359,7 @@ __global__ void __launch_bounds__(kSWarps * 32, V == 4 ? 6 : 4)
             }
             if (has_dv && R.nsub > 0) {
                 const float *vrow = dvin + R.cell_off;
-                const int vs = mod_n(c0, n);
+                const int vs = c0 < 0 ? c0 + n : c0;
                 for (int c = lane; c < L::Wv / 4; c += 32) {
                     int idx = vs + 4 * c;
                     if (idx >= n) idx -= n;
@@ -459,16 +446,13 @@ __global__ void __launch_bounds__(kSWarps * 32, V == 4 ? 6 : 4)
         issue_next();
     }
     if (__any_sync(0xffffffffu, cmax > 1.0f) && lane == 0) atomicOr(a.err, ERR_CFL);
-    // the parameter kernel launched before this one may still be running; the
-    // launches after this one must see it finished
-    pdl_wait();
 }
 
 template <int ORDER, int V>
 cudaError_t launch_stream_v(const Plan &p, const StepArgs &a, cudaStream_t s)
 {
     using L = SLayout<V>;
-    const int n_list = (int)p.stream_rows_h[ORDER].size();
+    const int n_list = (int)p.rows_seg_h[0][ORDER].size();
     if (n_list == 0) return cudaSuccess;
     const int umin = 64 * V - 2 * kSHaloMax;
     const int pairs_per_row = (p.stream_nmax[ORDER] + umin - 1) / umin;
@@ -489,8 +473,8 @@ cudaError_t launch_stream_v(const Plan &p, const StepArgs &a, cudaStream_t s)
     long long grid = (total + kSWarps - 1) / kSWarps;
     if (grid > (long long)sms * fit) grid = (long long)sms * fit;
     return launch_pdl(k_stream<ORDER, V>, (int)grid, kSWarps * 32, smem, s, a,
-                      static_cast<const StreamRow *>(p.stream_rows[ORDER]), n_list,
-                      pairs_per_row);
+                      static_cast<const int32_t *>(p.rows_seg[0][ORDER]), n_list, pairs_per_row,
+                      static_cast<const RowParams<float> *>(p.row_par));
 }
 
 }  // namespace

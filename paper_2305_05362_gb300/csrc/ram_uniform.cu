@@ -190,7 +190,7 @@ cudaError_t launch_order(const Plan &p, const StepArgs &a, cudaStream_t s)
     const bool vec_ok = aligned16(a.q_in) && aligned16(a.dv) && aligned16(a.q_out);
     if (!vec_ok)
         return launch_tiles<T, ORDER>(p, a, s, p.tiles_uniform[ORDER], p.tiles_uniform_h[ORDER]);
-    if (d == 0 && p.uniform_kernel[0] == 2 && !p.stream_rows_h[ORDER].empty()) {
+    if (d == 0 && p.uniform_kernel[0] == 2 && !p.rows_seg_h[0][ORDER].empty()) {
         // streaming warps: the same rows as the warp-segment kernel (16-byte aligned,
         // at least 512 cells: no shorter than the staged window of 4 cells per lane)
         cudaError_t e = launch_stream(p, a, s, ORDER);
