@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "ram_device.cuh"
+#include "ram_lane.cuh"
 #include "ram_tma.cuh"
 
 namespace ram {
@@ -34,237 +35,6 @@ constexpr int kMaxStagesH = 3;
 constexpr int kBatch = 32;  // rows whose parameters the producer warp computes at once
 // shared-memory header: barriers and the row parameters
 constexpr int kHeader = (6 * 8 + (kMaxStagesH + kBatch) * 80 + 127) / 128 * 128;
-
-template <typename T>
-__device__ __forceinline__ T half_vl(T dl, T dr)
-{
-    // half of the van Leer slope: dl dr / (dl + dr) when dl dr > 0, else 0
-    const T p = dl * dr;
-    return p > T(0) ? Num<T>::div(p, dl + dr) : T(0);
-}
-
-// Q' for V consecutive output cells.  q[0..V+4] holds source cells p0-2..p0+V+2
-// where p0 = m0 - K - 1 is the source cell of the left part of output cell m0:
-// Q'_m = (Q_p - A_p) + A_{p+1}, A the left partial integral at the edge offset.
-//
-// PPM (App. A) in difference form: with dif_i = Q_{i+1} - Q_i, D = dif_{i-1} +
-// dif_i and E_i = 2 (dQ_{i+1} - dQ_i),
-//   2 dQ_i = sign(D) min(|D|, 4 |dif_{i-1}|, 4 |dif_i|) if dif_{i-1} dif_i > 0 else 0,
-//   a = QR - Q = dif_i / 2 - E_i / 12,   b = Q - QL = dif_{i-1} / 2 + E_{i-1} / 12,
-// and the App. A.2 constraints (a b <= 0: flat; |b| > 2|a|: QL = 3Q - 2QR;
-// |a| > 2|b|: QR = 3Q - 2QL) are a' = median(0, a, 2b), b' = median(0, b, 2a).
-// The folded coefficients give A = xi Q + cR a' - cL b' (P.c[3] = xi, P.c[1] = cR,
-// P.c[0] = cL).
-template <typename T, int ORDER, int V>
-__device__ __forceinline__ void remap_group(const T (&q)[V + 5], const RowParams<T> &P, bool lim,
-                                            T (&out)[V])
-{
-    if (P.whole) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) out[k] = q[k + 3];
-        return;
-    }
-    T A[V + 1];
-    if (ORDER == 3) {
-        T dif[V + 4];
-#pragma unroll
-        for (int i = 0; i < V + 4; ++i) dif[i] = q[i + 1] - q[i];
-        T Dq[V + 3];  // 2 dQ of source cells p0-1 .. p0+V+1
-#pragma unroll
-        for (int i = 0; i < V + 3; ++i) {
-            const T D = dif[i] + dif[i + 1];
-            if (lim) {
-                const T m = fmax(fmin(fabs(D), T(4) * minxs(dif[i], dif[i + 1])), T(0));
-                Dq[i] = minxs(D, m);
-            } else {
-                Dq[i] = D;
-            }
-        }
-        T E[V + 2];
-#pragma unroll
-        for (int i = 0; i < V + 2; ++i) E[i] = Dq[i + 1] - Dq[i];
-        const T xi = P.c[3], cR = P.c[1], cL = P.c[0];
-#pragma unroll
-        for (int j = 0; j <= V; ++j) {
-            const T a = fma(E[j + 1], T(-1) / T(12), T(0.5) * dif[j + 2]);
-            const T b = fma(E[j], T(1) / T(12), T(0.5) * dif[j + 1]);
-            T G;
-            if (lim) {
-                const T a2 = fma(E[j + 1], T(-1) / T(6), dif[j + 2]);  // 2a
-                const T b2 = fma(E[j], T(1) / T(6), dif[j + 1]);       // 2b
-                const T u = fmax(minxs(a, b2), T(0));                  // |a'|
-                const T v = fmax(minxs(b, a2), T(0));                  // |b'|
-                G = xorsign(fma(cR, u, -cL * v), a);
-            } else {
-                G = fma(cR, a, -cL * b);
-            }
-            A[j] = fma(xi, q[j + 2], G);
-        }
-    } else if (ORDER == 2) {
-#pragma unroll
-        for (int j = 0; j <= V; ++j) {
-            const T dn = q[j + 2] - q[j + 1], up = q[j + 3] - q[j + 2];
-            const T sl = lim ? T(2) * half_vl(dn, up) : T(0.5) * (dn + up);
-            A[j] = fma(q[j + 2], P.c[0], sl * P.c[1]);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j <= V; ++j)
-            A[j] = P.c[0] * q[j] + P.c[1] * q[j + 1] + P.c[2] * q[j + 2] + P.c[3] * q[j + 3] +
-                   P.c[4] * q[j + 4];
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) out[k] = (q[k + 2] - A[k]) + A[k + 1];
-}
-
-// One residual sub-step for V cells m0..m0+V-1.  z[0..V+3] holds Q at cells
-// m0-2..m0+V+1, v[0..V] the interface velocities at m0..m0+V (interface k is the
-// left node of cell m0+k).  The flux through interface k (Eq. 6 with the PLM
-// slope of Sec. 3.1 for van Leer, none for donor) carries the upwind value at the
-// midpoint of the swept region:
-//   F = c+ (Q_{k-1} + h_{k-1} (1 - c+)) + c- (Q_k - h_k (1 + c-)),
-// c = v cf, c+ = max(c, 0), c- = c - c+, h the half van Leer slope.  cmax keeps
-// the largest |c| (the CFL check).
-template <typename T, int V>
-__device__ __forceinline__ void residual_group(const T (&z)[V + 4], const T (&v)[V + 1], T cf,
-                                               bool vl, T &cmax, T (&out)[V])
-{
-    T h[V + 2];  // half slopes of cells m0-1..m0+V
-    if (vl) {
-        T d[V + 3];
-#pragma unroll
-        for (int i = 0; i < V + 3; ++i) d[i] = z[i + 1] - z[i];
-#pragma unroll
-        for (int c = 0; c < V + 2; ++c) h[c] = half_vl(d[c], d[c + 1]);
-    }
-    T F[V + 1];
-#pragma unroll
-    for (int k = 0; k <= V; ++k) {
-        const T c = v[k] * cf;
-        const T ap = fmax(c, T(0));
-        const T am = c - ap;
-        cmax = fmax(cmax, fabs(c));
-        T f = fma(ap, z[k + 1], am * z[k + 2]);
-        if (vl) {
-            const T wp = fma(-ap, ap, ap);   // c+ (1 - c+)
-            const T wm = fma(-am, am, -am);  // -c- (1 + c-)
-            f = fma(wp, h[k], fma(wm, h[k + 1], f));
-        }
-        F[k] = f;
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) out[k] = z[k + 2] - (F[k + 1] - F[k]);
-}
-
-template <typename T>
-__device__ __forceinline__ T lim_dq(T dn, T up, bool lim)
-{
-    // delta<Q> of App. A on a uniform row from the two one-sided differences,
-    // limited by App. A.2: sign * min(|d|, 2|dn|, 2|up|) where dn up > 0, else 0
-    const T d = T(0.5) * (dn + up);
-    if (!lim) return d;
-    const T mm = fmin(fabs(dn), fabs(up));
-    const T m = fmin(fabs(d), mm + mm);
-    return (dn * up > T(0)) ? copysign(m, d) : T(0);
-}
-
-// The same two operations in compare-and-select form, for FP64 rows (whose
-// arithmetic runs on the FP64 pipe, where the min/max form saves nothing and
-// needs more registers).
-//
-// Q' for V consecutive output cells.  q[0..V+4] holds source cells p0-2..p0+V+2
-// where p0 = m0 - K - 1 is the source cell of the left part of output cell m0.
-// P.c holds the coefficients of the left partial at the edge offset xi; for PPM
-// they are folded with Q6 = 6Q - 3(QL + QR):  A = QL c0 + QR c1 + Q c2.
-template <typename T, int ORDER, int V>
-__device__ __forceinline__ void remap_group_cs(const T (&q)[V + 5], const RowParams<T> &P, bool lim,
-                                            T (&out)[V])
-{
-    if (P.whole) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) out[k] = q[k + 3];
-        return;
-    }
-    T A[V + 1];
-    if (ORDER == 3) {
-        T dif[V + 4];
-#pragma unroll
-        for (int k = 0; k < V + 4; ++k) dif[k] = q[k + 1] - q[k];
-        T dq[V + 3];
-#pragma unroll
-        for (int c = 1; c <= V + 3; ++c) dq[c - 1] = lim_dq(dif[c - 1], dif[c], lim);
-        T face[V + 2];
-        const T sixth = T(1) / T(6);
-#pragma unroll
-        for (int f = 0; f < V + 2; ++f)
-            face[f] = fma(T(0.5), dif[f + 1], q[f + 1]) - (dq[f + 1] - dq[f]) * sixth;
-#pragma unroll
-        for (int j = 0; j <= V; ++j) {
-            const T Q = q[j + 2];
-            T L = face[j], R = face[j + 1];
-            if (lim) {
-                // App. A.2 with a = QR - Q, b = Q - QL: flat at an extremum (a b <= 0);
-                // otherwise the parabola overshoots on the left when |b| > 2|a|
-                // (QL = 3Q - 2QR) and on the right when |a| > 2|b| (QR = 3Q - 2QL).
-                const T a = R - Q, b = Q - L;
-                const bool flat = a * b <= T(0);
-                const bool left = fabs(b) > T(2) * fabs(a);
-                const bool right = fabs(a) > T(2) * fabs(b);
-                const T L2 = left ? fma(T(-2), a, Q) : L;
-                const T R2 = right ? fma(T(2), b, Q) : R;
-                L = flat ? Q : L2;
-                R = flat ? Q : R2;
-            }
-            A[j] = fma(L, P.c[0], fma(R, P.c[1], Q * P.c[2]));
-        }
-    } else if (ORDER == 2) {
-#pragma unroll
-        for (int j = 0; j <= V; ++j) {
-            const T dn = q[j + 2] - q[j + 1], up = q[j + 3] - q[j + 2];
-            const T sl = lim ? T(2) * half_vl(dn, up) : T(0.5) * (dn + up);
-            A[j] = fma(q[j + 2], P.c[0], sl * P.c[1]);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j <= V; ++j)
-            A[j] = P.c[0] * q[j] + P.c[1] * q[j + 1] + P.c[2] * q[j + 2] + P.c[3] * q[j + 3] +
-                   P.c[4] * q[j + 4];
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) out[k] = (q[k + 2] - A[k]) + A[k + 1];
-}
-
-// One residual sub-step for V cells m0..m0+V-1.  z[0..V+3] holds Q at cells
-// m0-2..m0+V+1, v[0..V] the interface velocities at m0..m0+V (interface k is the
-// left node of cell m0+k).  Donor: the flux carries the upwind value; van Leer:
-// the upwind value corrected by the half slope at the midpoint of the swept
-// region (Eq. 6 with the PLM slope of Sec. 3.1).
-template <typename T, int V>
-__device__ __forceinline__ void residual_group_cs(const T (&z)[V + 4], const T (&v)[V + 1], T cf,
-                                               bool vl, bool &cfl_bad, T (&out)[V])
-{
-    T hs[V + 2];  // half slopes of cells m0-1..m0+V
-    if (vl) {
-#pragma unroll
-        for (int c = 0; c < V + 2; ++c) hs[c] = half_vl(z[c + 1] - z[c], z[c + 2] - z[c + 1]);
-    }
-    T F[V + 1];
-#pragma unroll
-    for (int k = 0; k <= V; ++k) {
-        const T c = v[k] * cf;
-        const bool pos = c > T(0);
-        const T Qu = pos ? z[k + 1] : z[k + 2];
-        T qh = Qu;
-        if (vl) {
-            const T h = pos ? hs[k] : hs[k + 1];
-            qh = Qu + h * ((pos ? T(1) : T(-1)) - c);
-        }
-        F[k] = c * qh;
-        cfl_bad |= fabs(c) > T(1);
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) out[k] = z[k + 2] - (F[k + 1] - F[k]);
-}
 
 // Write V results of the group starting at m0 into a ping-pong row buffer, with
 // the cyclic halo copies of the first and last kHaloP cells.

@@ -44,6 +44,7 @@ extern "C" ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out)
     out->rows_ctas_per_sm_f32 = p->rows_cps[0];
     out->rows_ctas_per_sm_f64 = p->rows_cps[1];
     out->stream_cells_per_lane_f32 = p->stream_v;
+    out->seg_cells_per_lane_f32 = p->seg_v;
     return RAM_OK;
 }
 
@@ -58,6 +59,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     bool sv = false;
     for (int i = 0; i < kStreamVCount; ++i) sv |= t->stream_cells_per_lane_f32 == kStreamVCandidates[i];
     if (!sv) return RAM_ERR_ARG;
+    if (t->seg_cells_per_lane_f32 != 8 && t->seg_cells_per_lane_f32 != 16) return RAM_ERR_ARG;
     if (t->rows_ctas_per_sm_f32 < 1 || t->rows_ctas_per_sm_f32 > 4 || t->rows_ctas_per_sm_f64 != 1)
         return RAM_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(plan);
@@ -72,6 +74,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     p->rows_cps[0] = t->rows_ctas_per_sm_f32;
     p->rows_cps[1] = t->rows_ctas_per_sm_f64;
     p->stream_v = t->stream_cells_per_lane_f32;
+    p->seg_v = t->seg_cells_per_lane_f32;
     return RAM_OK;
 }
 
@@ -116,17 +119,20 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
     if (any_rows || any_seg) {
         // candidates: (kernel, cells per thread)
         int best_k = p->uniform_kernel[d], best_v = p->rows_v[d], best_c = p->rows_cps[d];
-        int best_sv = p->stream_v;
+        int best_sv = p->stream_v, best_gv = p->seg_v;
         float best = 3.4e38f;
-        if (any_seg) {
-            p->uniform_kernel[d] = 1;
-            float ms = 0;
-            st = time_once(&ms);
-            if (st == RAM_OK && ms < best) {
-                best = ms;
-                best_k = 1;
+        if (any_seg)
+            for (int gv = 8; gv <= (d == 0 ? 16 : 8) && st == RAM_OK; gv += 8) {
+                p->uniform_kernel[d] = 1;
+                p->seg_v = gv;
+                float ms = 0;
+                st = time_once(&ms);
+                if (st == RAM_OK && ms < best) {
+                    best = ms;
+                    best_k = 1;
+                    best_gv = gv;
+                }
             }
-        }
         if (any_seg && d == 0)
             for (int i = 0; i < kStreamVCount && st == RAM_OK; ++i) {
                 p->uniform_kernel[0] = 2;
@@ -161,6 +167,7 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
         p->rows_v[d] = best_v;
         p->rows_cps[d] = best_c;
         p->stream_v = best_sv;
+        p->seg_v = best_gv;
     }
     if (any_tiles && st == RAM_OK) {
         const int tcs[] = {256, 512, 1024, 2048};

@@ -17,81 +17,10 @@
 #include <cstdint>
 #include <type_traits>
 
-#include "ram_device.cuh"
+#include "ram_lane.cuh"
 
 namespace ram {
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T half_vl2(T dl, T dr)
-{
-    const T p = dl * dr;
-    return p > T(0) ? Num<T>::div(p, dl + dr) : T(0);
-}
-
-template <typename T>
-__device__ __forceinline__ T lim_dq2(T dn, T up, bool lim)
-{
-    const T d = T(0.5) * (dn + up);
-    if (!lim) return d;
-    const T mm = fmin(fabs(dn), fabs(up));
-    const T m = fmin(fabs(d), mm + mm);
-    return (dn * up > T(0)) ? copysign(m, d) : T(0);
-}
-
-// Q' of V output cells from q[0..V+4] = source cells p0-2..p0+V+2 (same algebra as
-// the whole-row kernel: right part of p plus left part of p+1).
-template <typename T, int ORDER, int V>
-__device__ __forceinline__ void remap_v(const T (&q)[V + 5], const RowParams<T> &P, bool lim,
-                                        T (&out)[V])
-{
-    if (P.whole) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) out[k] = q[k + 3];
-        return;
-    }
-    T A[V + 1];
-    if (ORDER == 3) {
-        T dif[V + 4];
-#pragma unroll
-        for (int k = 0; k < V + 4; ++k) dif[k] = q[k + 1] - q[k];
-        T dq[V + 3];
-#pragma unroll
-        for (int c = 1; c <= V + 3; ++c) dq[c - 1] = lim_dq2(dif[c - 1], dif[c], lim);
-        const T sixth = T(1) / T(6);
-#pragma unroll
-        for (int j = 0; j <= V; ++j) {
-            const T Q = q[j + 2];
-            T L = fma(T(0.5), dif[j + 1], q[j + 1]) - (dq[j + 1] - dq[j]) * sixth;
-            T R = fma(T(0.5), dif[j + 2], q[j + 2]) - (dq[j + 2] - dq[j + 1]) * sixth;
-            if (lim) {
-                const T a = R - Q, b = Q - L;
-                const bool flat = a * b <= T(0);
-                const bool left = fabs(b) > T(2) * fabs(a);
-                const bool right = fabs(a) > T(2) * fabs(b);
-                const T L2 = left ? fma(T(-2), a, Q) : L;
-                const T R2 = right ? fma(T(2), b, Q) : R;
-                L = flat ? Q : L2;
-                R = flat ? Q : R2;
-            }
-            A[j] = fma(L, P.c[0], fma(R, P.c[1], Q * P.c[2]));
-        }
-    } else if (ORDER == 2) {
-#pragma unroll
-        for (int j = 0; j <= V; ++j) {
-            const T dn = q[j + 2] - q[j + 1], up = q[j + 3] - q[j + 2];
-            const T sl = lim ? T(2) * half_vl2(dn, up) : T(0.5) * (dn + up);
-            A[j] = fma(q[j + 2], P.c[0], sl * P.c[1]);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j <= V; ++j)
-            A[j] = P.c[0] * q[j] + P.c[1] * q[j + 1] + P.c[2] * q[j + 2] + P.c[3] * q[j + 3] +
-                   P.c[4] * q[j + 4];
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) out[k] = (q[k + 2] - A[k]) + A[k + 1];
-}
 
 __device__ __forceinline__ int wrap2(int c, int N)
 {
@@ -103,8 +32,14 @@ __device__ __forceinline__ int wrap2(int c, int N)
     return c;
 }
 
-template <typename T, int ORDER, int V>
-__global__ void __launch_bounds__(256, 3)
+// Index i in [0, 2N) brought into [0, N): one compare for the vectors of a
+// lane's window once its start is in [0, N).
+__device__ __forceinline__ int wrap1(int i, int N) { return i >= N ? i - N : i; }
+
+// LIM: limiters on; VL: van Leer residual (else donor) -- compile-time so that
+// the per-cell code carries no flag tests.
+template <typename T, int ORDER, int V, bool LIM, bool VL>
+__global__ void __launch_bounds__(256, V * sizeof(T) <= 32 ? 3 : 2)
     k_useg(StepArgs a, const int32_t *row_ids, const RowParams<T> *pars)
 {
     static_assert(V % (16 / sizeof(T)) == 0, "V must be a whole number of 16-byte vectors");
@@ -119,8 +54,8 @@ __global__ void __launch_bounds__(256, 3)
     const RowParams<T> P = pars[r];
     const int N = P.n;
     const int nsub = P.nsub;
-    const bool lim = a.limiter != 0;
-    const bool vl = a.scheme == RAM_VANLEER;
+    constexpr bool lim = LIM;
+    constexpr bool vl = VL;
     const int R = vl ? 2 : 1;
     // halo cells per warp end, rounded to whole vectors so that lanes stay aligned
     const int H4 = ((nsub * R + VEC - 1) / VEC) * VEC;
@@ -131,7 +66,7 @@ __global__ void __launch_bounds__(256, 3)
     T *qout = static_cast<T *>(a.q_out) + P.cell_off;
     // source window offset inside a 16-byte vector (the same for every lane)
     const int off = ((-P.K - 1) % VEC + VEC) % VEC;
-    bool cfl_bad = false;
+    T cmax = T(0);
 
     for (int seg = warp; seg < nseg; seg += nwarps) {
         const int out0 = seg * stride;               // first output cell of the segment
@@ -141,9 +76,10 @@ __global__ void __launch_bounds__(256, 3)
         const int base = p0 - off - VEC;             // vector aligned, <= p0 - 2
         constexpr int NW = V + 3 * VEC;              // loaded cells base .. base+NW-1
         T w[NW];
+        const int b0 = wrap2(base, N);
 #pragma unroll
         for (int c = 0; c < NW / VEC; ++c) {
-            const int idx = wrap2(base + c * VEC, N);
+            const int idx = wrap1(b0 + c * VEC, N);
             const Vec v = *reinterpret_cast<const Vec *>(qin + idx);
             if (sizeof(T) == 4) {
                 const float4 f4 = *reinterpret_cast<const float4 *>(&v);
@@ -188,7 +124,10 @@ __global__ void __launch_bounds__(256, 3)
             }
         }
         T cur[V];
-        remap_v<T, ORDER, V>(q, P, lim, cur);
+        if (sizeof(T) == 4)
+            remap_group<T, ORDER, V>(q, P, lim, cur);
+        else
+            remap_group_cs<T, ORDER, V>(q, P, lim, cur);
 
         // ---- residual sub-steps with shuffled two-cell halos ----
         if (nsub > 0) {
@@ -196,7 +135,7 @@ __global__ void __launch_bounds__(256, 3)
             const int vi = wrap2(m0, N);
 #pragma unroll
             for (int c = 0; c < V / VEC; ++c) {
-                const Vec vv = *reinterpret_cast<const Vec *>(dvp + wrap2(vi + c * VEC, N));
+                const Vec vv = *reinterpret_cast<const Vec *>(dvp + wrap1(vi + c * VEC, N));
                 if (sizeof(T) == 4) {
                     const float4 f4 = *reinterpret_cast<const float4 *>(&vv);
                     v[c * VEC + 0] = (T)f4.x;
@@ -219,37 +158,24 @@ __global__ void __launch_bounds__(256, 3)
                 for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
                 z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
                 z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
-                T hs[V + 2];
-                if (vl) {
-#pragma unroll
-                    for (int c = 0; c < V + 2; ++c)
-                        hs[c] = half_vl2(z[c + 1] - z[c], z[c + 2] - z[c + 1]);
+                if (sizeof(T) == 4) {
+                    residual_group<T, V>(z, v, cf, vl, cmax, cur);
+                } else {
+                    bool bad = false;
+                    residual_group_cs<T, V>(z, v, cf, vl, bad, cur);
+                    if (bad) cmax = T(2);
                 }
-                T F[V + 1];
-#pragma unroll
-                for (int k = 0; k <= V; ++k) {
-                    const T c = v[k] * cf;
-                    const bool pos = c > T(0);
-                    const T Qu = pos ? z[k + 1] : z[k + 2];
-                    T qh = Qu;
-                    if (vl) {
-                        const T h = pos ? hs[k] : hs[k + 1];
-                        qh = Qu + h * ((pos ? T(1) : T(-1)) - c);
-                    }
-                    F[k] = c * qh;
-                    cfl_bad |= fabs(c) > T(1);
-                }
-#pragma unroll
-                for (int k = 0; k < V; ++k) cur[k] = z[k + 2] - (F[k + 1] - F[k]);
             }
         }
 
         // ---- store the interior [H4, H4 + stride) of the segment, cells < N ----
+        // H4, stride, out0 and N are whole vectors, so every vector of the lane is
+        // either wholly stored or wholly halo: no scalar tail
         const int li0 = lane * V;                    // local index of cur[0]
-        const bool full = li0 >= H4 && li0 + V <= H4 + stride && out0 - H4 + li0 + V <= N;
-        if (full) {
 #pragma unroll
-            for (int c = 0; c < V / VEC; ++c) {
+        for (int c = 0; c < V / VEC; ++c) {
+            const int li = li0 + c * VEC;
+            if (li >= H4 && li < H4 + stride && m0 + c * VEC < N) {
                 Vec vv;
                 if (sizeof(T) == 4) {
                     float4 f4 = make_float4((float)cur[c * VEC], (float)cur[c * VEC + 1],
@@ -261,37 +187,51 @@ __global__ void __launch_bounds__(256, 3)
                 }
                 *reinterpret_cast<Vec *>(qout + m0 + c * VEC) = vv;
             }
-        } else {
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const int li = li0 + k;
-                const int g = out0 - H4 + li;
-                if (li >= H4 && li < H4 + stride && g < N) qout[g] = cur[k];
-            }
         }
     }
-    if (cfl_bad) atomicOr(a.err, ERR_CFL);
+    if (cmax > T(1)) atomicOr(a.err, ERR_CFL);
+}
+
+template <typename T, int ORDER, int V>
+cudaError_t launch_useg_v(const StepArgs &a, cudaStream_t s, const int32_t *row_ids, int n_rows,
+                          const RowParams<T> *par)
+{
+    const int threads = 256;
+    const bool lim = a.limiter != 0, vl = a.scheme == RAM_VANLEER;
+    if (lim && vl)
+        return launch_pdl(k_useg<T, ORDER, V, true, true>, n_rows, threads, 0, s, a, row_ids, par);
+    if (lim)
+        return launch_pdl(k_useg<T, ORDER, V, true, false>, n_rows, threads, 0, s, a, row_ids, par);
+    if (vl)
+        return launch_pdl(k_useg<T, ORDER, V, false, true>, n_rows, threads, 0, s, a, row_ids, par);
+    return launch_pdl(k_useg<T, ORDER, V, false, false>, n_rows, threads, 0, s, a, row_ids, par);
 }
 
 }  // namespace
 
-// Rows for this kernel: the plan's whole-row list (16-byte aligned rows) whose
-// length is at least two warp segments; V = 8 (FP32) / 4 (FP64) cells per lane.
+// Rows for this kernel: the plan's warp-segment list (16-byte aligned rows of at
+// least 512 cells, so that a lane's window wraps the row at most once); V = 8 or
+// 16 (FP32, the plan's choice) / 4 (FP64) cells per lane.
 cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
                         int order, const int32_t *row_ids, int n_rows)
 {
     if (n_rows == 0) return cudaSuccess;
-    const int threads = 256;
     const RowParams<float> *pf = static_cast<const RowParams<float> *>(p.row_par);
     const RowParams<double> *pd = static_cast<const RowParams<double> *>(p.row_par);
     if (dt == RAM_F32) {
-        if (order == 2) return launch_pdl(k_useg<float, 2, 8>, n_rows, threads, 0, s, a, row_ids, pf);
-        if (order == 3) return launch_pdl(k_useg<float, 3, 8>, n_rows, threads, 0, s, a, row_ids, pf);
-        return launch_pdl(k_useg<float, 4, 8>, n_rows, threads, 0, s, a, row_ids, pf);
+        const bool v16 = p.seg_v == 16;
+        if (order == 2)
+            return v16 ? launch_useg_v<float, 2, 16>(a, s, row_ids, n_rows, pf)
+                       : launch_useg_v<float, 2, 8>(a, s, row_ids, n_rows, pf);
+        if (order == 3)
+            return v16 ? launch_useg_v<float, 3, 16>(a, s, row_ids, n_rows, pf)
+                       : launch_useg_v<float, 3, 8>(a, s, row_ids, n_rows, pf);
+        return v16 ? launch_useg_v<float, 4, 16>(a, s, row_ids, n_rows, pf)
+                   : launch_useg_v<float, 4, 8>(a, s, row_ids, n_rows, pf);
     }
-    if (order == 2) return launch_pdl(k_useg<double, 2, 4>, n_rows, threads, 0, s, a, row_ids, pd);
-    if (order == 3) return launch_pdl(k_useg<double, 3, 4>, n_rows, threads, 0, s, a, row_ids, pd);
-    return launch_pdl(k_useg<double, 4, 4>, n_rows, threads, 0, s, a, row_ids, pd);
+    if (order == 2) return launch_useg_v<double, 2, 4>(a, s, row_ids, n_rows, pd);
+    if (order == 3) return launch_useg_v<double, 3, 4>(a, s, row_ids, n_rows, pd);
+    return launch_useg_v<double, 4, 4>(a, s, row_ids, n_rows, pd);
 }
 
 }  // namespace ram
