@@ -45,10 +45,11 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _workload(name, rank):
+def _workload(name, rank, disk=None):
     from paper_2305_05362_gb300 import workloads as wl
     if name == "disk":
-        return wl.disk(n_r=1024, n_phi=4096, seed_dv=4 + rank, dtype=np.float32)
+        n_r, n_phi = (1024, 4096) if disk is None else disk
+        return wl.disk(n_r=n_r, n_phi=n_phi, seed_dv=4 + rank, dtype=np.float32)
     if name == "disk_large":
         return wl.disk(n_r=8192, n_phi=16384, seed_dv=4 + rank, dtype=np.float32)
     if name == "batched":
@@ -145,7 +146,7 @@ def _kernel_name(tuning):
     if k == 0:
         return "k_rows<float,3,%d>" % tuning["rows_cells_per_thread_f32"]
     if k == 1:
-        return "k_useg<float,3,8>"
+        return "k_useg<float,3,%d,true,true>" % tuning["seg_cells_per_lane_f32"]
     return "k_stream<3,%d>" % tuning["stream_cells_per_lane_f32"]
 
 
@@ -175,7 +176,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = _workload(args.workload, 0)
+    w = _workload(args.workload, 0,
+                  tuple(int(x) for x in args.disk.split(",")) if args.disk else None)
     res = cpu_baseline(w, budget_s=max(2.0, 20.0 / max(1, args.steps)))
     steps = args.steps
     # each timed step is a bounded sample: the same oracle steps as cpu_baseline
@@ -220,6 +222,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=50)
+    ap.add_argument("--tuning", default=None,
+                    help="launch shapes as JSON (the tuning dict of an earlier line) instead of "
+                         "running the autotuner, e.g. to profile the exact kernels of a run")
+    ap.add_argument("--disk", default=None,
+                    help="rings,cells of the disk workload (default 1024,4096), e.g. for a "
+                         "profiling case above L2 but far below the large disk")
+    ap.add_argument("--no-hold", action="store_true",
+                    help="do not hold the GPU while the timed loop is queued (profiling only)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -237,12 +247,14 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = _workload(args.workload, rank)
+    disk = tuple(int(x) for x in args.disk.split(",")) if args.disk else None
+    w = _workload(args.workload, rank, disk)
     plan = ram.Plan.from_workload(w, device=local)
     info = plan.info()
+    # kernels of this library per step: the parameter kernel, then one launch per
+    # order present among the uniform rows, plus the non-uniform tiles' kernel
     uniform_orders = {int(o) for r, o in enumerate(w.order)} if info.n_uniform_rows else set()
-    launches_per_step = max(1, len(uniform_orders) if info.n_tiles_general == 0 else
-                            len(set(int(o) for o in w.order)) + 1)
+    launches_per_step = 1 + len(uniform_orders) + (1 if info.n_tiles_general else 0)
 
     def tensors(dtype):
         q = torch.tensor(np.asarray(w.q0), dtype=dtype, device=dev)
@@ -252,12 +264,18 @@ def main():
     v0 = torch.tensor(w.v0, dtype=torch.float64, device=dev)
     nsub = torch.tensor(w.nsub, dtype=torch.int32, device=dev)
     # autotune the launch shapes once for each dtype (outside the timed region)
-    for dt_ in (torch.float64, torch.float32):
-        q_ = torch.tensor(np.asarray(w.q0), dtype=dt_, device=dev)
-        dv_ = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dt_, device=dev)
-        ram.autotune(plan, q_, torch.empty_like(q_), v0, w.dt, dv=dv_, scheme=w.scheme,
-                     nsub=nsub, reps=10)
-        del q_, dv_
+    if args.tuning:
+        t = plan.tuning()
+        for k, v in json.loads(args.tuning).items():
+            setattr(t, k, int(v))
+        plan.set_tuning(t)
+    else:
+        for dt_ in (torch.float64, torch.float32):
+            q_ = torch.tensor(np.asarray(w.q0), dtype=dt_, device=dev)
+            dv_ = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dt_, device=dev)
+            ram.autotune(plan, q_, torch.empty_like(q_), v0, w.dt, dv=dv_, scheme=w.scheme,
+                         nsub=nsub, reps=10)
+            del q_, dv_
     tuning = plan.tuning().as_dict()
     props = torch.cuda.get_device_properties(dev)
     l2 = int(getattr(props, "L2_cache_size", 0) or 0)
@@ -289,7 +307,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         hold_s = min(20.0, 2.0 * host_per_step * steps + 0.05)
-        torch.cuda._sleep(int(hold_s * 2.1e9))
+        if not args.no_hold:
+            torch.cuda._sleep(int(hold_s * 2.1e9))
         for k in range(steps):
             do_flush()
             ev[k][0].record()
@@ -373,7 +392,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(_workload(args.workload, 0))
+        cpu = cpu_baseline(_workload(args.workload, 0, disk))
 
     if rank == 0:
         line = {
@@ -389,11 +408,14 @@ def main():
                        "parallelism": "dp%d (independent disks per GPU)" % world,
                        "tuning": tuning},
             "gpu_launches": int(args.steps * launches_per_step),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": kernel_key,
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "bytes_per_cell": bpc,
                          "traffic": None if tr is None else tr["dram_bytes_per_launch"]},
             "fp64_single": {"value": fp64_value, "unit": UNIT, "steps": n64,
+                            "form": "the same step in FP64 (cells and arithmetic), "
+                                    "autotuned, one launch per step",
                             "rel_l1_fp32_vs_fp64": rel},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "device_status": st,
         }
