@@ -237,7 +237,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2305_05362_gb300 import ram
+    from paper_2305_05362_gb300 import ram, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -335,10 +335,7 @@ def main():
     clocks = sampler.stop() if rank == 0 else None
     st = plan.check_errors()
     total_s = sum(ms32) / 1e3
-    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_max = float(t.item())
+    total_max = shard.global_max(total_s)  # max over ranks (NCCL, host scalar)
     cells_all = w.n_cells * world
     value = cells_all * args.steps / total_max / 1e9
     ms_per_step = 1e3 * total_max / args.steps
