@@ -171,7 +171,8 @@ typedef struct {
     int32_t rows_ctas_per_sm_f64;       /* whole-row kernel, FP64: 1 */
     int32_t stream_cells_per_lane_f32;  /* streaming-warp kernel, FP32: 4 or 8 cells per
                                            lane and segment (8 needs rows >= 520 cells) */
-    int32_t seg_cells_per_lane_f32;     /* warp-segment kernel, FP32: 8 or 16 */
+    int32_t seg_prefetch_f32;           /* warp-segment kernel, FP32: 1 = the loads of a
+                                           warp's next segment in flight while it computes */
 } ram_tuning;
 
 ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out);
@@ -182,7 +183,7 @@ ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *tuning);
  * on the caller's buffers -- the arguments of ram_step, without the phase --
  * with CUDA events on `stream` (`reps` timed steps per candidate) and keeps the
  * fastest in the plan.  Candidates: for uniform rows the warp-segment kernel
- * (FP32: 8 or 16 cells per lane),
+ * (FP32: with and without prefetch),
  * for FP32 the streaming-warp kernel with 4 or 8 cells per lane, and the
  * persistent whole-row kernel with (cells per thread, CTAs per SM) in
  * {5,7,9,11,15} x {2,3,4} as the register budget allows; tile cells

@@ -119,7 +119,7 @@ struct Plan {
     int32_t stream_nmax[5] = {0};
     int32_t stream_nmin[5] = {0};
     int32_t stream_v = 8;          // cells per lane of the streaming kernel
-    int32_t seg_v = 8;             // cells per lane of the warp-segment kernel (FP32)
+    int32_t seg_prefetch = 0;      // warp-segment kernel (FP32): next segment's loads in flight
     // 0: persistent whole-row, 1: warp segments, 2: streaming warps (FP32 only)
     int32_t uniform_kernel[2] = {1, 1};
     int32_t n_uniform_rows = 0;

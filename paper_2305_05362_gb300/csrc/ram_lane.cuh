@@ -250,4 +250,172 @@ __device__ __forceinline__ void residual_group_cs(const T (&z)[V + 4], const T (
 }
 
 
+// ---------------------------------------------------------------------------
+// Packed FP32 forms: two segments per lane, one per half of a float2.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// Q' for the V output cells of one lane in two segments at once (the two halves
+// of float2 registers: FP32 arithmetic on the packed pipe).  q[0..V+4] holds
+// source cells p0-2 .. p0+V+2 with p0 = m0 - K - 1, m0 the lane's first cell;
+// k holds the partial-integral coefficients (order 3: xi, cR, -cL; order 2:
+// xi, slope; order 4: the five weights).
+template <int ORDER, int V>
+__device__ __forceinline__ void remap_pair(const float2 (&q)[V + 5], int whole, const float (&k)[5],
+                                           bool lim, float2 (&out)[V])
+{
+    if (whole) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = q[k + 3];
+        return;
+    }
+    float2 A[V + 1];  // left partial integral of source cells p0 .. p0+V
+    if (ORDER == 3) {
+        float2 dif[V + 4];
+#pragma unroll
+        for (int i = 0; i < V + 4; ++i) dif[i] = sub2(q[i + 1], q[i]);
+        float2 Dq[V + 3];  // 2 dQ of source cells p0-1 .. p0+V+1
+#pragma unroll
+        for (int i = 0; i < V + 3; ++i) {
+            const float2 D = __fadd2_rn(dif[i], dif[i + 1]);
+            if (lim) {
+                float2 t = make_float2(minxs(dif[i].x, dif[i + 1].x), minxs(dif[i].y, dif[i + 1].y));
+                t = __fmul2_rn(t, f2(4.0f));
+                // minxs(D, m) = sign(D) min(|D|, m) for m >= 0
+                Dq[i] = make_float2(minxs(D.x, fmaxf(t.x, 0.0f)), minxs(D.y, fmaxf(t.y, 0.0f)));
+            } else {
+                Dq[i] = D;
+            }
+        }
+        float2 E[V + 2];  // 2 (dQ_{j+1} - dQ_j) for j = p0-1 .. p0+V
+#pragma unroll
+        for (int i = 0; i < V + 2; ++i) E[i] = sub2(Dq[i + 1], Dq[i]);
+        float2 h[V + 3];  // dif / 2 (index 1 .. V+2 used)
+#pragma unroll
+        for (int i = 1; i < V + 3; ++i) h[i] = __fmul2_rn(dif[i], f2(0.5f));
+        const float2 k0 = f2(k[0]), k1 = f2(k[1]), k2 = f2(k[2]);
+#pragma unroll
+        for (int j = 0; j <= V; ++j) {
+            // a = QR - Q = dif_j / 2 - E_j / 12,  b = Q - QL = dif_{j-1} / 2 + E_{j-1} / 12
+            const float2 a = __ffma2_rn(E[j + 1], f2(-1.0f / 12.0f), h[j + 2]);
+            const float2 b = __ffma2_rn(E[j], f2(1.0f / 12.0f), h[j + 1]);
+            float2 G;
+            if (lim) {
+                const float2 a2 = __ffma2_rn(E[j + 1], f2(-1.0f / 6.0f), dif[j + 2]);
+                const float2 b2 = __ffma2_rn(E[j], f2(1.0f / 6.0f), dif[j + 1]);
+                const float2 u = make_float2(fmaxf(minxs(a.x, b2.x), 0.0f),
+                                             fmaxf(minxs(a.y, b2.y), 0.0f));  // |a'|
+                const float2 v = make_float2(fmaxf(minxs(b.x, a2.x), 0.0f),
+                                             fmaxf(minxs(b.y, a2.y), 0.0f));  // |b'|
+                G = __ffma2_rn(k1, u, __fmul2_rn(k2, v));
+                G = make_float2(xorsign(G.x, a.x), xorsign(G.y, a.y));
+            } else {
+                G = __ffma2_rn(k1, a, __fmul2_rn(k2, b));
+            }
+            A[j] = __ffma2_rn(k0, q[j + 2], G);
+        }
+    } else if (ORDER == 2) {
+        const float2 k0 = f2(k[0]), k1 = f2(k[1]);
+#pragma unroll
+        for (int j = 0; j <= V; ++j) {
+            const float2 dn = sub2(q[j + 2], q[j + 1]), up = sub2(q[j + 3], q[j + 2]);
+            float2 sl;
+            if (lim) {
+                const float2 p = __fmul2_rn(dn, up);
+                const float2 s = __fadd2_rn(dn, up);
+                const float2 hh = __fmul2_rn(p, make_float2(__fdividef(2.0f, s.x),
+                                                            __fdividef(2.0f, s.y)));
+                sl = make_float2(p.x > 0.0f ? hh.x : 0.0f, p.y > 0.0f ? hh.y : 0.0f);
+            } else {
+                sl = __fmul2_rn(__fadd2_rn(dn, up), f2(0.5f));
+            }
+            A[j] = __ffma2_rn(q[j + 2], k0, __fmul2_rn(sl, k1));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j <= V; ++j) {
+            float2 s = __fmul2_rn(f2(k[0]), q[j]);
+#pragma unroll
+            for (int i = 1; i < 5; ++i) s = __ffma2_rn(f2(k[i]), q[j + i], s);
+            A[j] = s;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = __fadd2_rn(sub2(q[k + 2], A[k]), A[k + 1]);
+}
+
+// The residual sub-steps (Eq. 6) of one lane's cells in both segments.  v[0..V]
+// are the velocities at the lane's nodes m0..m0+V (node k is the left node of
+// cell m0+k).  The flux through node k is
+//   F = c+ (Q_{k-1} + h_{k-1} (1 - c+)) + c- (Q_k - h_k (1 + c-)),
+// c+ = max(c, 0), c- = min(c, 0), c = v cf, h the half van Leer slope (0 for
+// donor): the upwind value at the midpoint of the swept region.
+template <int V>
+__device__ __forceinline__ void residual_pair(float2 (&cur)[V], const float2 (&v)[V + 1], float cf,
+                                              int nsub, bool vl, int lane, float &cmax)
+{
+    float2 ap[V + 1], am[V + 1];
+#pragma unroll
+    for (int k = 0; k <= V; ++k) {
+        const float2 c = __fmul2_rn(v[k], f2(cf));
+        ap[k] = make_float2(fmaxf(c.x, 0.0f), fmaxf(c.y, 0.0f));
+        am[k] = sub2(c, ap[k]);
+        cmax = fmaxf(cmax, fmaxf(fabsf(c.x), fabsf(c.y)));
+    }
+    const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
+    for (int sub = 0; sub < nsub; ++sub) {
+        float2 z[V + 4];  // cells m0-2 .. m0+V+1
+        {
+            // lane 0's B continues lane 31's A; lane 31's A continues lane 0's B
+            const float l2x = __shfl_sync(0xffffffffu, cur[V - 2].x, up);
+            const float l2y = __shfl_sync(0xffffffffu, cur[V - 2].y, up);
+            const float l1x = __shfl_sync(0xffffffffu, cur[V - 1].x, up);
+            const float l1y = __shfl_sync(0xffffffffu, cur[V - 1].y, up);
+            const float r1x = __shfl_sync(0xffffffffu, cur[0].x, dn);
+            const float r1y = __shfl_sync(0xffffffffu, cur[0].y, dn);
+            const float r2x = __shfl_sync(0xffffffffu, cur[1].x, dn);
+            const float r2y = __shfl_sync(0xffffffffu, cur[1].y, dn);
+            z[0] = make_float2(l2x, lane == 0 ? l2x : l2y);
+            z[1] = make_float2(l1x, lane == 0 ? l1x : l1y);
+            z[V + 2] = make_float2(lane == 31 ? r1y : r1x, r1y);
+            z[V + 3] = make_float2(lane == 31 ? r2y : r2x, r2y);
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
+        float2 F[V + 1];
+        if (vl) {
+            float2 d[V + 3];
+#pragma unroll
+            for (int i = 0; i < V + 3; ++i) d[i] = sub2(z[i + 1], z[i]);
+            float2 h[V + 2];  // half slopes of cells m0-1 .. m0+V
+#pragma unroll
+            for (int c = 0; c < V + 2; ++c) {
+                const float2 p = __fmul2_rn(d[c], d[c + 1]);
+                const float2 s = __fadd2_rn(d[c], d[c + 1]);
+                // max(p, 0) / (s + tiny): the half slope without a select (see half_vl_relu)
+                const float2 st = __fadd2_rn(s, f2(1e-30f));
+                h[c] = __fmul2_rn(make_float2(fmaxf(p.x, 0.0f), fmaxf(p.y, 0.0f)),
+                                  make_float2(__fdividef(1.0f, st.x), __fdividef(1.0f, st.y)));
+            }
+#pragma unroll
+            for (int k = 0; k <= V; ++k) {
+                // c+ (1 - c+) and -c- (1 + c-) = c- (-1 - c-)
+                const float2 wp = __fmul2_rn(ap[k], __ffma2_rn(ap[k], f2(-1.0f), f2(1.0f)));
+                const float2 wm = __fmul2_rn(am[k], __ffma2_rn(am[k], f2(-1.0f), f2(-1.0f)));
+                float2 f = __fmul2_rn(am[k], z[k + 2]);
+                f = __ffma2_rn(ap[k], z[k + 1], f);
+                f = __ffma2_rn(wp, h[k], f);
+                F[k] = __ffma2_rn(wm, h[k + 1], f);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k <= V; ++k) F[k] = __ffma2_rn(ap[k], z[k + 1], __fmul2_rn(am[k], z[k + 2]));
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) cur[k] = sub2(z[k + 2], sub2(F[k + 1], F[k]));
+    }
+}
+
 }  // namespace ram

@@ -44,7 +44,7 @@ extern "C" ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out)
     out->rows_ctas_per_sm_f32 = p->rows_cps[0];
     out->rows_ctas_per_sm_f64 = p->rows_cps[1];
     out->stream_cells_per_lane_f32 = p->stream_v;
-    out->seg_cells_per_lane_f32 = p->seg_v;
+    out->seg_prefetch_f32 = p->seg_prefetch;
     return RAM_OK;
 }
 
@@ -59,7 +59,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     bool sv = false;
     for (int i = 0; i < kStreamVCount; ++i) sv |= t->stream_cells_per_lane_f32 == kStreamVCandidates[i];
     if (!sv) return RAM_ERR_ARG;
-    if (t->seg_cells_per_lane_f32 != 8 && t->seg_cells_per_lane_f32 != 16) return RAM_ERR_ARG;
+    if (t->seg_prefetch_f32 != 0 && t->seg_prefetch_f32 != 1) return RAM_ERR_ARG;
     if (t->rows_ctas_per_sm_f32 < 1 || t->rows_ctas_per_sm_f32 > 4 || t->rows_ctas_per_sm_f64 != 1)
         return RAM_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(plan);
@@ -74,7 +74,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     p->rows_cps[0] = t->rows_ctas_per_sm_f32;
     p->rows_cps[1] = t->rows_ctas_per_sm_f64;
     p->stream_v = t->stream_cells_per_lane_f32;
-    p->seg_v = t->seg_cells_per_lane_f32;
+    p->seg_prefetch = t->seg_prefetch_f32;
     return RAM_OK;
 }
 
@@ -119,12 +119,12 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
     if (any_rows || any_seg) {
         // candidates: (kernel, cells per thread)
         int best_k = p->uniform_kernel[d], best_v = p->rows_v[d], best_c = p->rows_cps[d];
-        int best_sv = p->stream_v, best_gv = p->seg_v;
+        int best_sv = p->stream_v, best_gv = p->seg_prefetch;
         float best = 3.4e38f;
         if (any_seg)
-            for (int gv = 8; gv <= (d == 0 ? 16 : 8) && st == RAM_OK; gv += 8) {
+            for (int gv = 0; gv <= (d == 0 ? 1 : 0) && st == RAM_OK; ++gv) {
                 p->uniform_kernel[d] = 1;
-                p->seg_v = gv;
+                p->seg_prefetch = gv;
                 float ms = 0;
                 st = time_once(&ms);
                 if (st == RAM_OK && ms < best) {
@@ -167,7 +167,7 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
         p->rows_v[d] = best_v;
         p->rows_cps[d] = best_c;
         p->stream_v = best_sv;
-        p->seg_v = best_gv;
+        p->seg_prefetch = best_gv;
     }
     if (any_tiles && st == RAM_OK) {
         const int tcs[] = {256, 512, 1024, 2048};

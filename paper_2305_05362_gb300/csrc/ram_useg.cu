@@ -192,6 +192,127 @@ __global__ void __launch_bounds__(256, V * sizeof(T) <= 32 ? 3 : 2)
     if (cmax > T(1)) atomicOr(a.err, ERR_CFL);
 }
 
+
+
+// The same step with the loads of a warp's next segment in flight while it
+// computes the current one (two register sets, the loop unrolled by two so the
+// sets swap roles without copies).  FP32 rows, 8 cells per lane.
+template <int ORDER, bool LIM, bool VL>
+__global__ void __launch_bounds__(256, 2)
+    k_useg_pf(StepArgs a, const int32_t *row_ids, const RowParams<float> *pars)
+{
+    constexpr int V = 8, VEC = 4, NW = V + 12;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    const int r = row_ids[blockIdx.x];
+    pdl_wait();
+    const RowParams<float> P = pars[r];
+    const int N = P.n;
+    const int nsub = P.nsub;
+    const int H4 = ((nsub * (VL ? 2 : 1) + VEC - 1) / VEC) * VEC;
+    const int stride = 32 * V - 2 * H4;
+    const int nseg = (N + stride - 1) / stride;
+    const float *qin = static_cast<const float *>(a.q_in) + P.cell_off;
+    const float *dvp = has_dv ? static_cast<const float *>(a.dv) + P.cell_off : nullptr;
+    float *qout = static_cast<float *>(a.q_out) + P.cell_off;
+    const int off = ((-P.K - 1) % VEC + VEC) % VEC;
+    const bool use_dv = has_dv && nsub > 0;
+    float cmax = 0.0f;
+
+    struct Raw {
+        float4 w[NW / VEC];
+        float4 v[V / VEC];
+    };
+    auto load = [&](int seg, Raw &x) {
+        const int m0 = seg * stride - H4 + lane * V;
+        const int b0 = wrap2(m0 - P.K - 1 - off - VEC, N);
+#pragma unroll
+        for (int c = 0; c < NW / VEC; ++c)
+            x.w[c] = *reinterpret_cast<const float4 *>(qin + wrap1(b0 + c * VEC, N));
+        if (use_dv) {
+            const int vi = wrap2(m0, N);
+#pragma unroll
+            for (int c = 0; c < V / VEC; ++c)
+                x.v[c] = *reinterpret_cast<const float4 *>(dvp + wrap1(vi + c * VEC, N));
+        }
+    };
+    auto compute = [&](int seg, const Raw &x) {
+        const int out0 = seg * stride;
+        const int m0 = out0 - H4 + lane * V;
+        float w[NW];
+#pragma unroll
+        for (int c = 0; c < NW / VEC; ++c) {
+            w[4 * c] = x.w[c].x;
+            w[4 * c + 1] = x.w[c].y;
+            w[4 * c + 2] = x.w[c].z;
+            w[4 * c + 3] = x.w[c].w;
+        }
+        float q[V + 5];
+        switch (off) {
+        case 0:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 2];
+            break;
+        case 1:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 3];
+            break;
+        case 2:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 4];
+            break;
+        default:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 5];
+            break;
+        }
+        float cur[V];
+        remap_group<float, ORDER, V>(q, P, LIM, cur);
+        if (use_dv) {
+            float v[V + 1];
+#pragma unroll
+            for (int c = 0; c < V / VEC; ++c) {
+                v[4 * c] = x.v[c].x;
+                v[4 * c + 1] = x.v[c].y;
+                v[4 * c + 2] = x.v[c].z;
+                v[4 * c + 3] = x.v[c].w;
+            }
+            v[V] = __shfl_down_sync(0xffffffffu, v[0], 1);
+            for (int sub = 0; sub < nsub; ++sub) {
+                float z[V + 4];
+                z[0] = __shfl_up_sync(0xffffffffu, cur[V - 2], 1);
+                z[1] = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+#pragma unroll
+                for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
+                z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
+                z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
+                residual_group<float, V>(z, v, P.cf, VL, cmax, cur);
+            }
+        }
+        const int li0 = lane * V;
+#pragma unroll
+        for (int c = 0; c < V / VEC; ++c) {
+            const int li = li0 + c * VEC;
+            if (li >= H4 && li < H4 + stride && m0 + c * VEC < N)
+                *reinterpret_cast<float4 *>(qout + m0 + c * VEC) =
+                    make_float4(cur[4 * c], cur[4 * c + 1], cur[4 * c + 2], cur[4 * c + 3]);
+        }
+    };
+
+    Raw ra, rb;
+    int seg = warp;
+    if (seg < nseg) load(seg, ra);
+    for (; seg < nseg; seg += 2 * nwarps) {
+        const int s1 = seg + nwarps, s2 = seg + 2 * nwarps;
+        if (s1 < nseg) load(s1, rb);
+        compute(seg, ra);
+        if (s2 < nseg) load(s2, ra);
+        if (s1 < nseg) compute(s1, rb);
+    }
+    if (cmax > 1.0f) atomicOr(a.err, ERR_CFL);
+}
+
 template <typename T, int ORDER, int V>
 cudaError_t launch_useg_v(const StepArgs &a, cudaStream_t s, const int32_t *row_ids, int n_rows,
                           const RowParams<T> *par)
@@ -207,11 +328,27 @@ cudaError_t launch_useg_v(const StepArgs &a, cudaStream_t s, const int32_t *row_
     return launch_pdl(k_useg<T, ORDER, V, false, false>, n_rows, threads, 0, s, a, row_ids, par);
 }
 
+template <int ORDER>
+cudaError_t launch_useg_pf(const StepArgs &a, cudaStream_t s, const int32_t *row_ids, int n_rows,
+                           const RowParams<float> *par)
+{
+    const int threads = 256;
+    const bool lim = a.limiter != 0, vl = a.scheme == RAM_VANLEER;
+    if (lim && vl)
+        return launch_pdl(k_useg_pf<ORDER, true, true>, n_rows, threads, 0, s, a, row_ids, par);
+    if (lim)
+        return launch_pdl(k_useg_pf<ORDER, true, false>, n_rows, threads, 0, s, a, row_ids, par);
+    if (vl)
+        return launch_pdl(k_useg_pf<ORDER, false, true>, n_rows, threads, 0, s, a, row_ids, par);
+    return launch_pdl(k_useg_pf<ORDER, false, false>, n_rows, threads, 0, s, a, row_ids, par);
+}
+
 }  // namespace
 
 // Rows for this kernel: the plan's warp-segment list (16-byte aligned rows of at
-// least 512 cells, so that a lane's window wraps the row at most once); V = 8 or
-// 16 (FP32, the plan's choice) / 4 (FP64) cells per lane.
+// least 512 cells, so that a lane's window wraps the row at most once); 8 (FP32)
+// or 4 (FP64) cells per lane; FP32 with or without the next segment's loads in
+// flight (the plan's choice).
 cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
                         int order, const int32_t *row_ids, int n_rows)
 {
@@ -219,15 +356,14 @@ cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStre
     const RowParams<float> *pf = static_cast<const RowParams<float> *>(p.row_par);
     const RowParams<double> *pd = static_cast<const RowParams<double> *>(p.row_par);
     if (dt == RAM_F32) {
-        const bool v16 = p.seg_v == 16;
-        if (order == 2)
-            return v16 ? launch_useg_v<float, 2, 16>(a, s, row_ids, n_rows, pf)
-                       : launch_useg_v<float, 2, 8>(a, s, row_ids, n_rows, pf);
-        if (order == 3)
-            return v16 ? launch_useg_v<float, 3, 16>(a, s, row_ids, n_rows, pf)
-                       : launch_useg_v<float, 3, 8>(a, s, row_ids, n_rows, pf);
-        return v16 ? launch_useg_v<float, 4, 16>(a, s, row_ids, n_rows, pf)
-                   : launch_useg_v<float, 4, 8>(a, s, row_ids, n_rows, pf);
+        if (p.seg_prefetch) {
+            if (order == 2) return launch_useg_pf<2>(a, s, row_ids, n_rows, pf);
+            if (order == 3) return launch_useg_pf<3>(a, s, row_ids, n_rows, pf);
+            return launch_useg_pf<4>(a, s, row_ids, n_rows, pf);
+        }
+        if (order == 2) return launch_useg_v<float, 2, 8>(a, s, row_ids, n_rows, pf);
+        if (order == 3) return launch_useg_v<float, 3, 8>(a, s, row_ids, n_rows, pf);
+        return launch_useg_v<float, 4, 8>(a, s, row_ids, n_rows, pf);
     }
     if (order == 2) return launch_useg_v<double, 2, 4>(a, s, row_ids, n_rows, pd);
     if (order == 3) return launch_useg_v<double, 3, 4>(a, s, row_ids, n_rows, pd);

@@ -336,9 +336,9 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
                                        oracle.shift_from_velocity(v0[r], dt), 3, True,
                                        dvr[r * n_phi:(r + 1) * n_phi], dt, scheme, int(nsub[r]))
                            for r in range(n_r)])
-    # kernels: 0 whole-row, 1 warp segments (FP32: V = 8, 16), 2 streaming warps
-    # (FP32; V = 4, 8)
-    for kern, sv in ((0, 8), (1, 8), (1, 16), (2, 4), (2, 8)):
+    # kernels: 0 whole-row, 1 warp segments (FP32: without / with prefetch),
+    # 2 streaming warps (FP32; V = 4, 8)
+    for kern, sv in ((0, 8), (1, 0), (1, 1), (2, 4), (2, 8)):
         if kern == 2 and dtype == "float64":
             continue
         t = plan.tuning()
@@ -346,8 +346,8 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
         t.uniform_kernel_f64 = min(kern, 1)
         if kern == 2:
             t.stream_cells_per_lane_f32 = sv
-        else:
-            t.seg_cells_per_lane_f32 = sv
+        elif kern == 1:
+            t.seg_prefetch_f32 = sv
         plan.set_tuning(t)
         out = torch.empty_like(qd)
         ram.step(plan, qd, out, _t(v0, torch.float64), dt, dv=dvd, scheme=scheme,
