@@ -36,163 +36,186 @@ __device__ __forceinline__ int wrap2(int c, int N)
 // lane's window once its start is in [0, N).
 __device__ __forceinline__ int wrap1(int i, int N) { return i >= N ? i - N : i; }
 
-// LIM: limiters on; VL: van Leer residual (else donor) -- compile-time so that
-// the per-cell code carries no flag tests.
+// One row's state for the warp-segment kernels.
+template <typename T>
+struct SegRow {
+    int N, nsub, H4, stride, nseg, off;
+    const T *qin, *dvp;
+    T *qout;
+};
+
+template <typename T, int V, bool VL>
+__device__ __forceinline__ void seg_row(const StepArgs &a, const RowParams<T> &P, SegRow<T> &S)
+{
+    constexpr int VEC = 16 / sizeof(T);
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    S.N = P.n;
+    S.nsub = P.nsub;
+    // halo cells per warp end, rounded to whole vectors so that lanes stay aligned
+    S.H4 = ((P.nsub * (VL ? 2 : 1) + VEC - 1) / VEC) * VEC;
+    S.stride = 32 * V - 2 * S.H4;  // output cells per warp segment
+    S.nseg = (S.N + S.stride - 1) / S.stride;
+    S.qin = static_cast<const T *>(a.q_in) + P.cell_off;
+    S.dvp = has_dv ? static_cast<const T *>(a.dv) + P.cell_off : nullptr;
+    S.qout = static_cast<T *>(a.q_out) + P.cell_off;
+    // source window offset inside a 16-byte vector (the same for every lane)
+    S.off = ((-P.K - 1) % VEC + VEC) % VEC;
+}
+
+// Segment seg of a row: this lane's V cells.
 template <typename T, int ORDER, int V, bool LIM, bool VL>
-__global__ void __launch_bounds__(256, V * sizeof(T) <= 32 ? 3 : 2)
-    k_useg(StepArgs a, const int32_t *row_ids, const RowParams<T> *pars)
+__device__ __forceinline__ void seg_step(const RowParams<T> &P, const SegRow<T> &S, int seg,
+                                         int lane, T &cmax)
 {
     static_assert(V % (16 / sizeof(T)) == 0, "V must be a whole number of 16-byte vectors");
     constexpr int VEC = 16 / sizeof(T);
     using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const int N = S.N, nsub = S.nsub, H4 = S.H4, stride = S.stride, off = S.off;
+    const T *qin = S.qin;
+    const T *dvp = S.dvp;
+    T *qout = S.qout;
+    constexpr bool lim = LIM;
+    constexpr bool vl = VL;
+    const int out0 = seg * stride;               // first output cell of the segment
+    const int m0 = out0 - H4 + lane * V;         // this lane's first cell (may wrap)
+    // ---- source window: cells p0-2 .. p0+V+2, p0 = m0 - K - 1 ----
+    const int p0 = m0 - P.K - 1;
+    const int base = p0 - off - VEC;             // vector aligned, <= p0 - 2
+    constexpr int NW = V + 3 * VEC;              // loaded cells base .. base+NW-1
+    T w[NW];
+    const int b0 = wrap2(base, N);
+#pragma unroll
+    for (int c = 0; c < NW / VEC; ++c) {
+        const int idx = wrap1(b0 + c * VEC, N);
+        const Vec v = *reinterpret_cast<const Vec *>(qin + idx);
+        if (sizeof(T) == 4) {
+            const float4 f4 = *reinterpret_cast<const float4 *>(&v);
+            w[c * VEC + 0] = (T)f4.x;
+            w[c * VEC + 1] = (T)f4.y;
+            w[c * VEC + 2] = (T)f4.z;
+            w[c * VEC + 3] = (T)f4.w;
+        } else {
+            const double2 d2 = *reinterpret_cast<const double2 *>(&v);
+            w[c * VEC + 0] = (T)d2.x;
+            w[c * VEC + 1] = (T)d2.y;
+        }
+    }
+    // q[j] = w[off + VEC - 2 + j]: a warp-uniform shift
+    T q[V + 5];
+    if (sizeof(T) == 4) {
+        switch (off) {
+        case 0:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 2];
+            break;
+        case 1:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 1];
+            break;
+        case 2:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC];
+            break;
+        default:
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC + 1];
+            break;
+        }
+    } else {
+        if (off == 0) {
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 2];
+        } else {
+#pragma unroll
+            for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 1];
+        }
+    }
+    T cur[V];
+    if (sizeof(T) == 4)
+        remap_group<T, ORDER, V>(q, P, lim, cur);
+    else
+        remap_group_cs<T, ORDER, V>(q, P, lim, cur);
+
+    // ---- residual sub-steps with shuffled two-cell halos ----
+    if (nsub > 0) {
+        T v[V + 1];
+        const int vi = wrap2(m0, N);
+#pragma unroll
+        for (int c = 0; c < V / VEC; ++c) {
+            const Vec vv = *reinterpret_cast<const Vec *>(dvp + wrap1(vi + c * VEC, N));
+            if (sizeof(T) == 4) {
+                const float4 f4 = *reinterpret_cast<const float4 *>(&vv);
+                v[c * VEC + 0] = (T)f4.x;
+                v[c * VEC + 1] = (T)f4.y;
+                v[c * VEC + 2] = (T)f4.z;
+                v[c * VEC + 3] = (T)f4.w;
+            } else {
+                const double2 d2 = *reinterpret_cast<const double2 *>(&vv);
+                v[c * VEC + 0] = (T)d2.x;
+                v[c * VEC + 1] = (T)d2.y;
+            }
+        }
+        v[V] = __shfl_down_sync(0xffffffffu, v[0], 1);
+        const T cf = P.cf;
+        for (int sub = 0; sub < nsub; ++sub) {
+            T z[V + 4];
+            z[0] = __shfl_up_sync(0xffffffffu, cur[V - 2], 1);
+            z[1] = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+#pragma unroll
+            for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
+            z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
+            z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
+            if (sizeof(T) == 4) {
+                residual_group<T, V>(z, v, cf, vl, cmax, cur);
+            } else {
+                bool bad = false;
+                residual_group_cs<T, V>(z, v, cf, vl, bad, cur);
+                if (bad) cmax = T(2);
+            }
+        }
+    }
+
+    // ---- store the interior [H4, H4 + stride) of the segment, cells < N ----
+    // H4, stride, out0 and N are whole vectors, so every vector of the lane is
+    // either wholly stored or wholly halo: no scalar tail
+    const int li0 = lane * V;                    // local index of cur[0]
+#pragma unroll
+    for (int c = 0; c < V / VEC; ++c) {
+        const int li = li0 + c * VEC;
+        if (li >= H4 && li < H4 + stride && m0 + c * VEC < N) {
+            Vec vv;
+            if (sizeof(T) == 4) {
+                float4 f4 = make_float4((float)cur[c * VEC], (float)cur[c * VEC + 1],
+                                        (float)cur[c * VEC + 2], (float)cur[c * VEC + 3]);
+                vv = *reinterpret_cast<Vec *>(&f4);
+            } else {
+                double2 d2 = make_double2((double)cur[c * VEC], (double)cur[c * VEC + 1]);
+                vv = *reinterpret_cast<Vec *>(&d2);
+            }
+            *reinterpret_cast<Vec *>(qout + m0 + c * VEC) = vv;
+        }
+    }
+}
+
+// LIM: limiters on; VL: van Leer residual (else donor) -- compile-time so that
+// the per-cell code carries no flag tests.  One CTA per row.
+template <typename T, int ORDER, int V, bool LIM, bool VL>
+__global__ void __launch_bounds__(256, V * sizeof(T) <= 32 ? 3 : 2)
+    k_useg(StepArgs a, const int32_t *row_ids, const RowParams<T> *pars)
+{
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
     const int r = row_ids[blockIdx.x];
     // the row's shift parameters come from the parameter kernel just before
     pdl_wait();
     const RowParams<T> P = pars[r];
-    const int N = P.n;
-    const int nsub = P.nsub;
-    constexpr bool lim = LIM;
-    constexpr bool vl = VL;
-    const int R = vl ? 2 : 1;
-    // halo cells per warp end, rounded to whole vectors so that lanes stay aligned
-    const int H4 = ((nsub * R + VEC - 1) / VEC) * VEC;
-    const int stride = 32 * V - 2 * H4;  // output cells per warp segment
-    const int nseg = (N + stride - 1) / stride;
-    const T *qin = static_cast<const T *>(a.q_in) + P.cell_off;
-    const T *dvp = has_dv ? static_cast<const T *>(a.dv) + P.cell_off : nullptr;
-    T *qout = static_cast<T *>(a.q_out) + P.cell_off;
-    // source window offset inside a 16-byte vector (the same for every lane)
-    const int off = ((-P.K - 1) % VEC + VEC) % VEC;
+    SegRow<T> S;
+    seg_row<T, V, VL>(a, P, S);
     T cmax = T(0);
-
-    for (int seg = warp; seg < nseg; seg += nwarps) {
-        const int out0 = seg * stride;               // first output cell of the segment
-        const int m0 = out0 - H4 + lane * V;         // this lane's first cell (may wrap)
-        // ---- source window: cells p0-2 .. p0+V+2, p0 = m0 - K - 1 ----
-        const int p0 = m0 - P.K - 1;
-        const int base = p0 - off - VEC;             // vector aligned, <= p0 - 2
-        constexpr int NW = V + 3 * VEC;              // loaded cells base .. base+NW-1
-        T w[NW];
-        const int b0 = wrap2(base, N);
-#pragma unroll
-        for (int c = 0; c < NW / VEC; ++c) {
-            const int idx = wrap1(b0 + c * VEC, N);
-            const Vec v = *reinterpret_cast<const Vec *>(qin + idx);
-            if (sizeof(T) == 4) {
-                const float4 f4 = *reinterpret_cast<const float4 *>(&v);
-                w[c * VEC + 0] = (T)f4.x;
-                w[c * VEC + 1] = (T)f4.y;
-                w[c * VEC + 2] = (T)f4.z;
-                w[c * VEC + 3] = (T)f4.w;
-            } else {
-                const double2 d2 = *reinterpret_cast<const double2 *>(&v);
-                w[c * VEC + 0] = (T)d2.x;
-                w[c * VEC + 1] = (T)d2.y;
-            }
-        }
-        // q[j] = w[off + VEC - 2 + j]: a warp-uniform shift
-        T q[V + 5];
-        if (sizeof(T) == 4) {
-            switch (off) {
-            case 0:
-#pragma unroll
-                for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 2];
-                break;
-            case 1:
-#pragma unroll
-                for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 1];
-                break;
-            case 2:
-#pragma unroll
-                for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC];
-                break;
-            default:
-#pragma unroll
-                for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC + 1];
-                break;
-            }
-        } else {
-            if (off == 0) {
-#pragma unroll
-                for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 2];
-            } else {
-#pragma unroll
-                for (int j = 0; j < V + 5; ++j) q[j] = w[j + VEC - 1];
-            }
-        }
-        T cur[V];
-        if (sizeof(T) == 4)
-            remap_group<T, ORDER, V>(q, P, lim, cur);
-        else
-            remap_group_cs<T, ORDER, V>(q, P, lim, cur);
-
-        // ---- residual sub-steps with shuffled two-cell halos ----
-        if (nsub > 0) {
-            T v[V + 1];
-            const int vi = wrap2(m0, N);
-#pragma unroll
-            for (int c = 0; c < V / VEC; ++c) {
-                const Vec vv = *reinterpret_cast<const Vec *>(dvp + wrap1(vi + c * VEC, N));
-                if (sizeof(T) == 4) {
-                    const float4 f4 = *reinterpret_cast<const float4 *>(&vv);
-                    v[c * VEC + 0] = (T)f4.x;
-                    v[c * VEC + 1] = (T)f4.y;
-                    v[c * VEC + 2] = (T)f4.z;
-                    v[c * VEC + 3] = (T)f4.w;
-                } else {
-                    const double2 d2 = *reinterpret_cast<const double2 *>(&vv);
-                    v[c * VEC + 0] = (T)d2.x;
-                    v[c * VEC + 1] = (T)d2.y;
-                }
-            }
-            v[V] = __shfl_down_sync(0xffffffffu, v[0], 1);
-            const T cf = P.cf;
-            for (int sub = 0; sub < nsub; ++sub) {
-                T z[V + 4];
-                z[0] = __shfl_up_sync(0xffffffffu, cur[V - 2], 1);
-                z[1] = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
-#pragma unroll
-                for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
-                z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
-                z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
-                if (sizeof(T) == 4) {
-                    residual_group<T, V>(z, v, cf, vl, cmax, cur);
-                } else {
-                    bool bad = false;
-                    residual_group_cs<T, V>(z, v, cf, vl, bad, cur);
-                    if (bad) cmax = T(2);
-                }
-            }
-        }
-
-        // ---- store the interior [H4, H4 + stride) of the segment, cells < N ----
-        // H4, stride, out0 and N are whole vectors, so every vector of the lane is
-        // either wholly stored or wholly halo: no scalar tail
-        const int li0 = lane * V;                    // local index of cur[0]
-#pragma unroll
-        for (int c = 0; c < V / VEC; ++c) {
-            const int li = li0 + c * VEC;
-            if (li >= H4 && li < H4 + stride && m0 + c * VEC < N) {
-                Vec vv;
-                if (sizeof(T) == 4) {
-                    float4 f4 = make_float4((float)cur[c * VEC], (float)cur[c * VEC + 1],
-                                            (float)cur[c * VEC + 2], (float)cur[c * VEC + 3]);
-                    vv = *reinterpret_cast<Vec *>(&f4);
-                } else {
-                    double2 d2 = make_double2((double)cur[c * VEC], (double)cur[c * VEC + 1]);
-                    vv = *reinterpret_cast<Vec *>(&d2);
-                }
-                *reinterpret_cast<Vec *>(qout + m0 + c * VEC) = vv;
-            }
-        }
-    }
+    for (int seg = warp; seg < S.nseg; seg += nwarps)
+        seg_step<T, ORDER, V, LIM, VL>(P, S, seg, lane, cmax);
     if (cmax > T(1)) atomicOr(a.err, ERR_CFL);
 }
-
-
 
 // The same step with the loads of a warp's next segment in flight while it
 // computes the current one (two register sets, the loop unrolled by two so the
