@@ -173,6 +173,7 @@ typedef struct {
                                            lane and segment (8 needs rows >= 520 cells) */
     int32_t seg_prefetch_f32;           /* warp-segment kernel, FP32: 1 = the loads of a
                                            warp's next segment in flight while it computes */
+    int32_t seg_warps;                  /* warp-segment kernel: warps per row CTA, 3..8 */
 } ram_tuning;
 
 ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out);
@@ -183,7 +184,7 @@ ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *tuning);
  * on the caller's buffers -- the arguments of ram_step, without the phase --
  * with CUDA events on `stream` (`reps` timed steps per candidate) and keeps the
  * fastest in the plan.  Candidates: for uniform rows the warp-segment kernel
- * (FP32: with and without prefetch),
+ * (3, 4, 6 or 8 warps per row CTA; FP32: with and without prefetch),
  * for FP32 the streaming-warp kernel with 4 or 8 cells per lane, and the
  * persistent whole-row kernel with (cells per thread, CTAs per SM) in
  * {5,7,9,11,15} x {2,3,4} as the register budget allows; tile cells

@@ -337,10 +337,10 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 template <typename T, int ORDER, int V>
-cudaError_t launch_useg_v(const StepArgs &a, cudaStream_t s, const int32_t *row_ids, int n_rows,
+cudaError_t launch_useg_v(const StepArgs &a, cudaStream_t s, int threads, const int32_t *row_ids,
+                          int n_rows,
                           const RowParams<T> *par)
 {
-    const int threads = 256;
     const bool lim = a.limiter != 0, vl = a.scheme == RAM_VANLEER;
     if (lim && vl)
         return launch_pdl(k_useg<T, ORDER, V, true, true>, n_rows, threads, 0, s, a, row_ids, par);
@@ -352,10 +352,10 @@ cudaError_t launch_useg_v(const StepArgs &a, cudaStream_t s, const int32_t *row_
 }
 
 template <int ORDER>
-cudaError_t launch_useg_pf(const StepArgs &a, cudaStream_t s, const int32_t *row_ids, int n_rows,
+cudaError_t launch_useg_pf(const StepArgs &a, cudaStream_t s, int threads, const int32_t *row_ids,
+                           int n_rows,
                            const RowParams<float> *par)
 {
-    const int threads = 256;
     const bool lim = a.limiter != 0, vl = a.scheme == RAM_VANLEER;
     if (lim && vl)
         return launch_pdl(k_useg_pf<ORDER, true, true>, n_rows, threads, 0, s, a, row_ids, par);
@@ -376,21 +376,24 @@ cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStre
                         int order, const int32_t *row_ids, int n_rows)
 {
     if (n_rows == 0) return cudaSuccess;
+    // warps per row CTA: a row's segments take ceil(segments / warps) rounds and the
+    // rows ceil(rows / resident CTAs) waves; the plan's choice trades the two
+    const int threads = 32 * p.seg_warps;
     const RowParams<float> *pf = static_cast<const RowParams<float> *>(p.row_par);
     const RowParams<double> *pd = static_cast<const RowParams<double> *>(p.row_par);
     if (dt == RAM_F32) {
         if (p.seg_prefetch) {
-            if (order == 2) return launch_useg_pf<2>(a, s, row_ids, n_rows, pf);
-            if (order == 3) return launch_useg_pf<3>(a, s, row_ids, n_rows, pf);
-            return launch_useg_pf<4>(a, s, row_ids, n_rows, pf);
+            if (order == 2) return launch_useg_pf<2>(a, s, threads, row_ids, n_rows, pf);
+            if (order == 3) return launch_useg_pf<3>(a, s, threads, row_ids, n_rows, pf);
+            return launch_useg_pf<4>(a, s, threads, row_ids, n_rows, pf);
         }
-        if (order == 2) return launch_useg_v<float, 2, 8>(a, s, row_ids, n_rows, pf);
-        if (order == 3) return launch_useg_v<float, 3, 8>(a, s, row_ids, n_rows, pf);
-        return launch_useg_v<float, 4, 8>(a, s, row_ids, n_rows, pf);
+        if (order == 2) return launch_useg_v<float, 2, 8>(a, s, threads, row_ids, n_rows, pf);
+        if (order == 3) return launch_useg_v<float, 3, 8>(a, s, threads, row_ids, n_rows, pf);
+        return launch_useg_v<float, 4, 8>(a, s, threads, row_ids, n_rows, pf);
     }
-    if (order == 2) return launch_useg_v<double, 2, 4>(a, s, row_ids, n_rows, pd);
-    if (order == 3) return launch_useg_v<double, 3, 4>(a, s, row_ids, n_rows, pd);
-    return launch_useg_v<double, 4, 4>(a, s, row_ids, n_rows, pd);
+    if (order == 2) return launch_useg_v<double, 2, 4>(a, s, threads, row_ids, n_rows, pd);
+    if (order == 3) return launch_useg_v<double, 3, 4>(a, s, threads, row_ids, n_rows, pd);
+    return launch_useg_v<double, 4, 4>(a, s, threads, row_ids, n_rows, pd);
 }
 
 }  // namespace ram

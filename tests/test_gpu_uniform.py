@@ -336,14 +336,16 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
                                        oracle.shift_from_velocity(v0[r], dt), 3, True,
                                        dvr[r * n_phi:(r + 1) * n_phi], dt, scheme, int(nsub[r]))
                            for r in range(n_r)])
-    # kernels: 0 whole-row, 1 warp segments (FP32: without / with prefetch),
-    # 2 streaming warps (FP32; V = 4, 8)
-    for kern, sv in ((0, 8), (1, 0), (1, 1), (2, 4), (2, 8)):
+    # kernels: 0 whole-row, 1 warp segments (FP32: without / with prefetch; 3-8
+    # warps per row CTA), 2 streaming warps (FP32; V = 4, 8)
+    for kern, sv, gw in ((0, 8, 8), (1, 0, 8), (1, 0, 3), (1, 1, 6), (1, 1, 4), (2, 4, 8),
+                         (2, 8, 8)):
         if kern == 2 and dtype == "float64":
             continue
         t = plan.tuning()
         t.uniform_kernel_f32 = kern
         t.uniform_kernel_f64 = min(kern, 1)
+        t.seg_warps = gw
         if kern == 2:
             t.stream_cells_per_lane_f32 = sv
         elif kern == 1:
@@ -357,5 +359,5 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
         for r in range(n_r):
             sl = slice(r * n_phi, (r + 1) * n_phi)
             err = np.sum(np.abs(got[sl] - refs[sl])) / np.sum(np.abs(refs[sl]))
-            assert err <= TOL[dtype], (kern, sv, r, err)
+            assert err <= TOL[dtype], (kern, sv, gw, r, err)
     assert plan.check_errors() == 0
