@@ -74,23 +74,6 @@ __device__ __forceinline__ double inv_small(int n)
     return t[n];
 }
 
-// The bulk displacement of this launch for row r (S0): the given shift, v0 dt,
-// or zero for the residual step alone.  A non-finite value is flagged and
-// replaced by zero.
-__device__ __forceinline__ double row_shift(const StepArgs &a, int r)
-{
-    double s = 0.0;
-    if (a.mode == MODE_SHIFT)
-        s = a.shift[r];
-    else if (a.mode == MODE_STEP)
-        s = __dmul_rn(a.v0[r], a.dt);
-    if (!isfinite(s)) {
-        atomicOr(a.err, ERR_NONFINITE);
-        s = 0.0;
-    }
-    return s;
-}
-
 // van Leer harmonic slope (Sec. 3.1) in undivided form (slope x width) on a
 // uniform row: 2 dl dr / (dl + dr) when dl dr > 0, else 0.
 template <typename T>
@@ -208,23 +191,35 @@ __device__ __forceinline__ void partial_coeffs(int order, U xi, T (&c)[5])
 }
 
 // The shift parameters of one row for one launch (S0), in FP64: the bulk
-// displacement s (row_shift), the accumulated phase (advanced by s when
-// update_phase), the fixed-point shift of rows with their own mesh, and for
-// uniform rows sig = (s mod L) N / L split into K = floor(sig) whole cells and
-// the fraction f, with the coefficients of the left partial integral at the
-// edge offset xi = 1 - f (partial_coeffs); and cf = dt / (nsub dx), the Courant number per unit dv of one residual
-// sub-step.  Returns xi.  Every kernel that needs these values computes them
-// with this function, so they agree bit for bit.
+// displacement s (the given shift, v0 dt, or zero for the residual step alone;
+// a non-finite value is flagged and replaced by zero), the accumulated phase
+// (advanced by s when update_phase), the fixed-point shift of rows with their
+// own mesh, and for uniform rows sig = (s mod L) N / L split into K = floor(sig)
+// whole cells and the fraction f, with the coefficients of the left partial
+// integral at the edge offset xi = 1 - f (partial_coeffs); and cf = dt / (nsub
+// dx), the Courant number per unit dv of one residual sub-step.  Returns xi.
+// Every kernel that needs these values computes them with this function, so
+// they agree bit for bit.
 template <typename T>
 __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo &row, int r,
                                                bool update_phase, RowParams<T> &P)
 {
+    // every global read of the row first, so that their latencies overlap (the
+    // parameter kernel runs on cold caches right before the row kernels)
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    const bool do_phase = update_phase && a.mode == MODE_STEP && a.phase != nullptr;
+    const double s_in = a.mode == MODE_SHIFT ? a.shift[r] : (a.mode == MODE_STEP ? a.v0[r] : 0.0);
+    const int ns_in = has_dv ? (a.nsub ? a.nsub[r] : 1) : 0;
+    const double ph_in = do_phase ? a.phase[r] : 0.0;
     const int N = row.n;
     P.cell_off = row.cell_off;
     P.n = N;
-    const double sft = row_shift(a, r);
-    if (update_phase && a.mode == MODE_STEP && a.phase != nullptr)
-        a.phase[r] = reduce_mod_rcp(a.phase[r] + sft, row.period, row.inv_period);
+    double sft = a.mode == MODE_STEP ? __dmul_rn(s_in, a.dt) : s_in;
+    if (!isfinite(sft)) {
+        atomicOr(a.err, ERR_NONFINITE);
+        sft = 0.0;
+    }
+    if (do_phase) a.phase[r] = reduce_mod_rcp(ph_in + sft, row.period, row.inv_period);
     const double sred = reduce_mod_rcp(sft, row.period, row.inv_period);
     // fixed-point shift for rows with their own mesh: nodes are stored as fractions
     // of the period in units of 2^-64, so x - s and the periodic wrap are exact
@@ -248,11 +243,10 @@ __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo 
         partial_coeffs<float>(row.order, (float)xi, P.c);
     else
         partial_coeffs<double>(row.order, xi, P.c);
-    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
     int nsub = 0;
     P.cf = T(0);
     if (has_dv) {
-        nsub = a.nsub ? a.nsub[r] : 1;
+        nsub = ns_in;
         if (nsub < 1 || nsub > RAM_MAX_NSUB) {
             atomicOr(a.err, ERR_NSUB);
             nsub = nsub < 1 ? 1 : RAM_MAX_NSUB;
