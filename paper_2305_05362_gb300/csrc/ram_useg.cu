@@ -83,11 +83,23 @@ __device__ __forceinline__ void seg_step(const RowParams<T> &P, const SegRow<T> 
     const int base = p0 - off - VEC;             // vector aligned, <= p0 - 2
     constexpr int NW = V + 3 * VEC;              // loaded cells base .. base+NW-1
     T w[NW];
-    const int b0 = wrap2(base, N);
+    Vec raw[NW / VEC];
+    // warp-uniform: when the warp's whole window lies inside the row (all but
+    // the segments at the row's ends), no lane's window wraps
+    const int wb = wrap2(out0 - H4 - P.K - 1 - off - VEC, N);
+    if (wb + 32 * V + NW <= N) {
+        const T *src = qin + wb + lane * V;
+#pragma unroll
+        for (int c = 0; c < NW / VEC; ++c) raw[c] = *reinterpret_cast<const Vec *>(src + c * VEC);
+    } else {
+        const int b0 = wrap2(base, N);
+#pragma unroll
+        for (int c = 0; c < NW / VEC; ++c)
+            raw[c] = *reinterpret_cast<const Vec *>(qin + wrap1(b0 + c * VEC, N));
+    }
 #pragma unroll
     for (int c = 0; c < NW / VEC; ++c) {
-        const int idx = wrap1(b0 + c * VEC, N);
-        const Vec v = *reinterpret_cast<const Vec *>(qin + idx);
+        const Vec v = raw[c];
         if (sizeof(T) == 4) {
             const float4 f4 = *reinterpret_cast<const float4 *>(&v);
             w[c * VEC + 0] = (T)f4.x;
@@ -139,10 +151,22 @@ __device__ __forceinline__ void seg_step(const RowParams<T> &P, const SegRow<T> 
     // ---- residual sub-steps with shuffled two-cell halos ----
     if (nsub > 0) {
         T v[V + 1];
-        const int vi = wrap2(m0, N);
+        Vec vraw[V / VEC];
+        const int wv = wrap2(out0 - H4, N);
+        if (wv + 32 * V <= N) {
+            const T *src = dvp + wv + lane * V;
+#pragma unroll
+            for (int c = 0; c < V / VEC; ++c)
+                vraw[c] = *reinterpret_cast<const Vec *>(src + c * VEC);
+        } else {
+            const int vi = wrap2(m0, N);
+#pragma unroll
+            for (int c = 0; c < V / VEC; ++c)
+                vraw[c] = *reinterpret_cast<const Vec *>(dvp + wrap1(vi + c * VEC, N));
+        }
 #pragma unroll
         for (int c = 0; c < V / VEC; ++c) {
-            const Vec vv = *reinterpret_cast<const Vec *>(dvp + wrap1(vi + c * VEC, N));
+            const Vec vv = vraw[c];
             if (sizeof(T) == 4) {
                 const float4 f4 = *reinterpret_cast<const float4 *>(&vv);
                 v[c * VEC + 0] = (T)f4.x;
@@ -248,16 +272,34 @@ __global__ void __launch_bounds__(256, 2)
         float4 v[V / VEC];
     };
     auto load = [&](int seg, Raw &x) {
-        const int m0 = seg * stride - H4 + lane * V;
-        const int b0 = wrap2(m0 - P.K - 1 - off - VEC, N);
+        const int w0 = seg * stride - H4;  // the warp's first cell
+        const int m0 = w0 + lane * V;
+        // warp-uniform: no lane's window wraps unless the segment is at a row end
+        const int wb = wrap2(w0 - P.K - 1 - off - VEC, N);
+        if (wb + 32 * V + NW <= N) {
+            const float *src = qin + wb + lane * V;
 #pragma unroll
-        for (int c = 0; c < NW / VEC; ++c)
-            x.w[c] = *reinterpret_cast<const float4 *>(qin + wrap1(b0 + c * VEC, N));
+            for (int c = 0; c < NW / VEC; ++c)
+                x.w[c] = *reinterpret_cast<const float4 *>(src + c * VEC);
+        } else {
+            const int b0 = wrap2(m0 - P.K - 1 - off - VEC, N);
+#pragma unroll
+            for (int c = 0; c < NW / VEC; ++c)
+                x.w[c] = *reinterpret_cast<const float4 *>(qin + wrap1(b0 + c * VEC, N));
+        }
         if (use_dv) {
-            const int vi = wrap2(m0, N);
+            const int wv = wrap2(w0, N);
+            if (wv + 32 * V <= N) {
+                const float *src = dvp + wv + lane * V;
 #pragma unroll
-            for (int c = 0; c < V / VEC; ++c)
-                x.v[c] = *reinterpret_cast<const float4 *>(dvp + wrap1(vi + c * VEC, N));
+                for (int c = 0; c < V / VEC; ++c)
+                    x.v[c] = *reinterpret_cast<const float4 *>(src + c * VEC);
+            } else {
+                const int vi = wrap2(m0, N);
+#pragma unroll
+                for (int c = 0; c < V / VEC; ++c)
+                    x.v[c] = *reinterpret_cast<const float4 *>(dvp + wrap1(vi + c * VEC, N));
+            }
         }
     };
     auto compute = [&](int seg, const Raw &x) {
