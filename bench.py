@@ -146,7 +146,7 @@ def _kernel_name(tuning):
     if k == 0:
         return "k_rows<float,3,%d>" % tuning["rows_cells_per_thread_f32"]
     if k == 1:
-        return ("k_useg_pf<3,true,true>" if tuning["seg_prefetch_f32"]
+        return ("k_useg_pf<3,true,true>" if tuning["seg_variant_f32"]
                 else "k_useg<float,3,8,true,true>")
     return "k_stream<3,%d>" % tuning["stream_cells_per_lane_f32"]
 

@@ -119,7 +119,8 @@ struct Plan {
     int32_t stream_nmax[5] = {0};
     int32_t stream_nmin[5] = {0};
     int32_t stream_v = 8;          // cells per lane of the streaming kernel
-    int32_t seg_prefetch = 0;      // warp-segment kernel (FP32): next segment's loads in flight
+    int32_t seg_variant = 0;       // warp-segment kernel (FP32): 1 = the next segment's
+                                   // loads in flight
     int32_t seg_warps = 8;         // warp-segment kernel: warps per row CTA (3..8)
     // 0: persistent whole-row, 1: warp segments, 2: streaming warps (FP32 only)
     int32_t uniform_kernel[2] = {1, 1};

@@ -44,7 +44,7 @@ extern "C" ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out)
     out->rows_ctas_per_sm_f32 = p->rows_cps[0];
     out->rows_ctas_per_sm_f64 = p->rows_cps[1];
     out->stream_cells_per_lane_f32 = p->stream_v;
-    out->seg_prefetch_f32 = p->seg_prefetch;
+    out->seg_variant_f32 = p->seg_variant;
     out->seg_warps = p->seg_warps;
     return RAM_OK;
 }
@@ -60,7 +60,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     bool sv = false;
     for (int i = 0; i < kStreamVCount; ++i) sv |= t->stream_cells_per_lane_f32 == kStreamVCandidates[i];
     if (!sv) return RAM_ERR_ARG;
-    if (t->seg_prefetch_f32 != 0 && t->seg_prefetch_f32 != 1) return RAM_ERR_ARG;
+    if (t->seg_variant_f32 != 0 && t->seg_variant_f32 != 1) return RAM_ERR_ARG;
     if (t->seg_warps < 3 || t->seg_warps > 8) return RAM_ERR_ARG;
     if (t->rows_ctas_per_sm_f32 < 1 || t->rows_ctas_per_sm_f32 > 4 || t->rows_ctas_per_sm_f64 != 1)
         return RAM_ERR_ARG;
@@ -76,7 +76,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     p->rows_cps[0] = t->rows_ctas_per_sm_f32;
     p->rows_cps[1] = t->rows_ctas_per_sm_f64;
     p->stream_v = t->stream_cells_per_lane_f32;
-    p->seg_prefetch = t->seg_prefetch_f32;
+    p->seg_variant = t->seg_variant_f32;
     p->seg_warps = t->seg_warps;
     return RAM_OK;
 }
@@ -122,14 +122,14 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
     if (any_rows || any_seg) {
         // candidates: (kernel, cells per thread)
         int best_k = p->uniform_kernel[d], best_v = p->rows_v[d], best_c = p->rows_cps[d];
-        int best_sv = p->stream_v, best_gv = p->seg_prefetch, best_gw = p->seg_warps;
+        int best_sv = p->stream_v, best_gv = p->seg_variant, best_gw = p->seg_warps;
         float best = 3.4e38f;
         if (any_seg)
             for (int gv = 0; gv <= (d == 0 ? 1 : 0) && st == RAM_OK; ++gv)
                 for (int gw : {3, 4, 6, 8}) {
                     if (st != RAM_OK) break;
                     p->uniform_kernel[d] = 1;
-                    p->seg_prefetch = gv;
+                    p->seg_variant = gv;
                     p->seg_warps = gw;
                     float ms = 0;
                     st = time_once(&ms);
@@ -174,7 +174,7 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
         p->rows_v[d] = best_v;
         p->rows_cps[d] = best_c;
         p->stream_v = best_sv;
-        p->seg_prefetch = best_gv;
+        p->seg_variant = best_gv;
         p->seg_warps = best_gw;
     }
     if (any_tiles && st == RAM_OK) {

@@ -424,7 +424,7 @@ cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStre
     const RowParams<float> *pf = static_cast<const RowParams<float> *>(p.row_par);
     const RowParams<double> *pd = static_cast<const RowParams<double> *>(p.row_par);
     if (dt == RAM_F32) {
-        if (p.seg_prefetch) {
+        if (p.seg_variant) {
             if (order == 2) return launch_useg_pf<2>(a, s, threads, row_ids, n_rows, pf);
             if (order == 3) return launch_useg_pf<3>(a, s, threads, row_ids, n_rows, pf);
             return launch_useg_pf<4>(a, s, threads, row_ids, n_rows, pf);

@@ -63,7 +63,7 @@ class Tuning(ctypes.Structure):
                 ("uniform_kernel_f32", ctypes.c_int32), ("uniform_kernel_f64", ctypes.c_int32),
                 ("rows_ctas_per_sm_f32", ctypes.c_int32), ("rows_ctas_per_sm_f64", ctypes.c_int32),
                 ("stream_cells_per_lane_f32", ctypes.c_int32),
-                ("seg_prefetch_f32", ctypes.c_int32), ("seg_warps", ctypes.c_int32)]
+                ("seg_variant_f32", ctypes.c_int32), ("seg_warps", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

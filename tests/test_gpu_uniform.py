@@ -349,7 +349,7 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
         if kern == 2:
             t.stream_cells_per_lane_f32 = sv
         elif kern == 1:
-            t.seg_prefetch_f32 = sv
+            t.seg_variant_f32 = sv
         plan.set_tuning(t)
         out = torch.empty_like(qd)
         ram.step(plan, qd, out, _t(v0, torch.float64), dt, dv=dvd, scheme=scheme,
