@@ -323,6 +323,33 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return q, ms
 
+    # The autotuner times warm-cache repeats; the timed steps run on a cold L2
+    # (flushed before each step), which can rank the warp-segment launch shapes
+    # differently.  Refine them under the bench's own protocol (median of 30
+    # flushed steps each) before the timed run.
+    if not args.tuning and info.n_uniform_rows == w.n_rows:
+        base = plan.tuning()
+        cands = [None] + [(v, g) for v in (0, 1) for g in (3, 4, 6, 8)]
+        best, best_ms = None, float("inf")
+        for c in cands:
+            t = plan.tuning()
+            for f, _ in t._fields_:
+                setattr(t, f, getattr(base, f))
+            if c is not None:
+                t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, c[0], c[1]
+            plan.set_tuning(t)
+            _, ms_c = timed(torch.float32, 30, 3)
+            med = statistics.median(ms_c)
+            if med < best_ms:
+                best, best_ms = c, med
+        t = plan.tuning()
+        for f, _ in t._fields_:
+            setattr(t, f, getattr(base, f))
+        if best is not None:
+            t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, best[0], best[1]
+        plan.set_tuning(t)
+        tuning = plan.tuning().as_dict()
+
     # FP32 timed run
     uuid = None
     try:
