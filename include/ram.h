@@ -139,6 +139,18 @@ ram_status ram_row_mass(ram_plan plan, ram_dtype dtype, const void *q, double *m
  * RAM_ERR_TIMEOUT. */
 ram_status ram_plan_check_errors(ram_plan plan);
 
+/* Failure-detection test hook.  Every device-side wait of the step kernels (the
+ * persistent whole-row kernel's waits for its staged rows and for free stages)
+ * is bounded: after `limit` tries (default 2^20) it gives up, records
+ * RAM_ERR_TIMEOUT in the error word and the CTA returns once its own copies in
+ * flight have landed, so a stalled pipeline ends the launch instead of hanging
+ * the GPU.  `limit` = 0 makes every such wait give up at once, which exercises
+ * that path deterministically: the next ram_plan_check_errors returns
+ * RAM_ERR_TIMEOUT and the step's output is undefined.  Other kernels have no
+ * waits and are unaffected.  Host only; applies to later launches of this plan.
+ * Returns RAM_ERR_ARG for a NULL plan. */
+ram_status ram_plan_set_wait_limit(ram_plan plan, uint32_t limit);
+
 typedef struct {
     int32_t n_rows;
     int64_t n_cells;

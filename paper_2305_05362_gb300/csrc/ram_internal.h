@@ -51,7 +51,11 @@ struct Tile {
     int32_t window;       // bound on the source-window cells (non-uniform tiles)
 };
 
+// Tries of a bounded device-side wait before it gives up and records a timeout.
+constexpr uint32_t kWaitLimit = 1u << 20;
+
 // Arguments shared by the step kernels (passed by value).
+
 struct StepArgs {
     const RowInfo *rows;
     const Tile *tiles;
@@ -73,6 +77,7 @@ struct StepArgs {
     const float *dx32;      // widths, FP32
     const double *dx64;     // widths, FP64
     const int32_t *buckets; // per-row bucket table: cell holding each bucket start
+    uint32_t wait_limit = kWaitLimit;  // tries of every bounded mbarrier wait
 };
 
 // Shift parameters of one uniform row for one launch (S0), written by the
@@ -126,6 +131,7 @@ struct Plan {
     int32_t uniform_kernel[2] = {1, 1};
     int32_t n_uniform_rows = 0;
     int32_t window_max = 0;        // max planned source window (non-uniform tiles)
+    uint32_t wait_limit = kWaitLimit;  // tries of the bounded waits (0: give up at once)
     // device
     RowInfo *rows = nullptr;
     Tile *tiles_uniform[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

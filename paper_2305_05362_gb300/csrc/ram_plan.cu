@@ -451,6 +451,13 @@ extern "C" ram_status ram_plan_set_tiling(ram_plan plan, int32_t tile_cells, int
     return st;
 }
 
+extern "C" ram_status ram_plan_set_wait_limit(ram_plan plan, uint32_t limit)
+{
+    if (!plan) return RAM_ERR_ARG;
+    reinterpret_cast<Plan *>(plan)->wait_limit = limit;
+    return RAM_OK;
+}
+
 extern "C" ram_status ram_plan_check_errors(ram_plan plan)
 {
     if (!plan) return RAM_ERR_ARG;

@@ -33,8 +33,8 @@ constexpr int kMaxStages = 3;
 constexpr int kMaxStagesH = 3;
 
 constexpr int kBatch = 32;  // rows whose parameters the producer warp computes at once
-// shared-memory header: barriers and the row parameters
-constexpr int kHeader = (6 * 8 + (kMaxStagesH + kBatch) * 80 + 127) / 128 * 128;
+// shared-memory header: barriers, the row parameters and the consumers' abort flag
+constexpr int kHeader = (6 * 8 + (kMaxStagesH + kBatch) * 80 + 4 + 127) / 128 * 128;
 
 // Write V results of the group starting at m0 into a ping-pong row buffer, with
 // the cyclic halo copies of the first and last kHaloP cells.
@@ -64,13 +64,15 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
            const RowParams<T> *pars)
 {
     static_assert(V + 3 <= kHaloS && V + 1 <= kHaloP, "halo too small for V");
-    static_assert(sizeof(RowParams<T>) <= 80 && kHeader % 128 == 0, "header layout");
+    static_assert(sizeof(RowParams<T>) <= 80 && kHeader % 128 == 0 &&
+                      6 * 8 + (kMaxStagesH + kBatch) * 80 + 4 <= kHeader,
+                  "header layout");
     static_assert((kHaloS * sizeof(T)) % 16 == 0 && (kHaloP * sizeof(T)) % 16 == 0,
                   "halos must keep 16-byte alignment");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int rowlen = ncap + 2 * kHaloS;  // staged row, with halos
     const int plen = ncap + 2 * kHaloP;    // ping-pong buffer
-    // layout: [mbar full x3][mbar empty x3][params x3][batch params x32]
+    // layout: [mbar full x3][mbar empty x3][params x3][batch params x32][abort]
     //         [Sq x stages][Sv x stages][A]
     // The residual sub-steps ping-pong between A and the stage's own Sq (free once
     // the remap has read it).
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
     uint64_t *empty = full + kMaxStages;
     RowParams<T> *par = reinterpret_cast<RowParams<T> *>(empty + kMaxStages);
     RowParams<T> *parb = par + kMaxStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(parb + kBatch);
     T *base = reinterpret_cast<T *>(smem_raw + kHeader);
     T *Sq = base;
     T *Sv = Sq + (size_t)stages * rowlen;
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
             mbar_init(&full[s], 2);  // copy (expect_tx) + parameters
             mbar_init(&empty[s], nwc);
         }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -108,6 +112,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
         const int my_rows = (n_rows - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         const uint32_t hb = kHaloS * sizeof(T);
         int issued = 0;  // rows whose copies were issued
+        int nfill = 0;   // fills issued (lane 0): fill f uses stage f % stages
         for (int kb = 0; kb < my_rows && ok; kb += kBatch) {
             const int k = kb + lane;
             const int kend = min(kb + kBatch, my_rows);
@@ -135,6 +140,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
                     tma_load(sv + kHaloS, dv, N * sizeof(T), &full[s]);
                     tma_load(sv + kHaloS + N, dv, hb, &full[s]);
                 }
+                ++nfill;
             };
             const int pre = min(kend, stages) - kb;  // copies that need no empty wait
             for (int j = 0; j < pre; ++j) {
@@ -151,7 +157,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
                 for (int kk = kb; kk < kend; ++kk) {
                     const int s = kk % stages;
                     if (kk >= issued) {
-                        if (kk >= stages && !mbar_wait(&empty[s], ((kk / stages) - 1) & 1)) {
+                        if (kk >= stages &&
+                            !mbar_wait(&empty[s], ((kk / stages) - 1) & 1, a.wait_limit)) {
                             atomicOr(a.err, ERR_TIMEOUT);
                             ok = false;
                             break;
@@ -165,9 +172,15 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             __syncwarp();
         }
-        // after a timeout, wait (bounded) for the copies already in flight
-        if (!ok && lane == 0)
-            for (int s = 0; s < stages; ++s) mbar_wait(&full[s], 0);
+        // No copy may still be landing when the CTA exits, and after a timeout
+        // the consumers may have returned without waiting for theirs: wait
+        // (bounded, with the default number of tries) for the last fill of every
+        // stage.  Each issued fill also got its parameter arrival, so its phase
+        // completes once its bytes land; the earlier fills of a stage completed
+        // before it could be refilled.
+        if (lane == 0)
+            for (int f = max(0, nfill - stages); f < nfill; ++f)
+                mbar_wait(&full[f % stages], (f / stages) & 1);
         return;
     }
 
@@ -179,15 +192,21 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
     int k = 0;
     for (int ri = blockIdx.x; ri < n_rows; ri += gridDim.x, ++k) {
         const int s = k % stages;
-        if (!mbar_wait(&full[s], (k / stages) & 1)) {
-            if (ct == 0) atomicOr(a.err, ERR_TIMEOUT);
-            return;
+        // A wait that runs out skips the remap and raises the abort flag; every
+        // consumer reads the flag after the same barrier, so all of them leave
+        // together (a consumer that left alone would stall the others at the
+        // next named barrier).  The flag of row k is read before the barrier
+        // that ends row k, and a timeout at row k+1 is raised only after it.
+        const bool got = mbar_wait(&full[s], (k / stages) & 1, a.wait_limit);
+        if (!got) {
+            *abort_flag = 1;
+            atomicOr(a.err, ERR_TIMEOUT);
         }
         const RowParams<T> P = par[s];
         const int N = P.n;
         T *sq = Sq + (size_t)s * rowlen + kHaloS;  // valid on [-kHaloS, N+kHaloS)
         const T *sv = Sv + (size_t)s * rowlen + kHaloS;  // valid on [0, N+16)
-        const int ngroups = (N + V - 1) / V;
+        const int ngroups = got ? (N + V - 1) / V : 0;
         const int nsub = P.nsub;
 
         // remap (Eqs. 18, 26): Q' of every group of V output cells into pa
@@ -206,6 +225,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 288 : 544,
             put_group<T, V>(pa, m0, N, out);
         }
         consumer_sync(nct);
+        if (*abort_flag) return;
 
         // residual sub-steps (Eq. 6), ping-pong between A and the staged row
         T *src = pa, *dst = sq;

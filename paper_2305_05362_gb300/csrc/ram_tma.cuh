@@ -9,9 +9,9 @@
 
 #include <cstdint>
 
-namespace ram {
+#include "ram_internal.h"
 
-constexpr uint32_t kWaitLimit = 1u << 20;
+namespace ram {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -24,10 +24,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Wait for the phase of parity `parity` to complete, trying at most `limit`
+// times (0: give up at once); true when it completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = kWaitLimit)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

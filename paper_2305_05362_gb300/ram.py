@@ -28,8 +28,8 @@ MAX_NSUB = 8
 
 EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwind",
            "ram_step", "ram_step_adjoint", "ram_row_mass", "ram_plan_check_errors",
-           "ram_plan_query", "ram_plan_set_tiling", "ram_plan_get_tuning",
-           "ram_plan_set_tuning", "ram_plan_autotune", "ram_step_uniform_noalloc",
+           "ram_plan_query", "ram_plan_set_tiling", "ram_plan_set_wait_limit",
+           "ram_plan_get_tuning", "ram_plan_set_tuning", "ram_plan_autotune", "ram_step_uniform_noalloc",
            "ram_status_string", "ram_version"]
 STATIC_MAX_ROWS = 4096
 
@@ -94,6 +94,7 @@ def load(path: Optional[str] = None):
     lib.ram_plan_check_errors.argtypes = [vp]
     lib.ram_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.ram_plan_set_tiling.argtypes = [vp, i32, i32]
+    lib.ram_plan_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
     lib.ram_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.ram_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.ram_plan_autotune.argtypes = [vp, i32, vp, vp, vp, f64, vp, i32, vp, i32, vp]
@@ -214,6 +215,12 @@ class Plan:
     def set_tuning(self, t: Tuning):
         _check(self._lib.ram_plan_set_tuning(self.handle, ctypes.byref(t)),
                "ram_plan_set_tuning")
+
+    def set_wait_limit(self, limit: int = 1 << 20):
+        """Tries of every bounded device-side wait (test hook; 0: give up at once,
+        so a step on the whole-row kernel records a timeout)."""
+        _check(self._lib.ram_plan_set_wait_limit(self.handle, int(limit)),
+               "ram_plan_set_wait_limit")
 
     def check_errors(self) -> int:
         """Synchronise and return (and clear) the device error status (0 = ok)."""

@@ -49,6 +49,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.ram_step(None, 0, None, None, None, None, ctypes.c_double(0.0), None, 0,
                         None, None) == 1
     assert lib.ram_plan_destroy(None) == 0
+    assert lib.ram_plan_set_wait_limit(None, 0) == 1
 
 
 def test_library_is_not_the_oracle():
