@@ -146,8 +146,8 @@ def _kernel_name(tuning):
     if k == 0:
         return "k_rows<float,3,%d>" % tuning["rows_cells_per_thread_f32"]
     if k == 1:
-        return ("k_useg_pf<3,true,true>" if tuning["seg_variant_f32"]
-                else "k_useg<float,3,8,true,true>")
+        return {1: "k_useg_pf<3,true,true>", 2: "k_useg_ring<3,8,true,true>"}.get(
+            tuning["seg_variant_f32"], "k_useg<float,3,8,true,true>")
     return "k_stream<3,%d>" % tuning["stream_cells_per_lane_f32"]
 
 
@@ -252,10 +252,18 @@ def main():
     w = _workload(args.workload, rank, disk)
     plan = ram.Plan.from_workload(w, device=local)
     info = plan.info()
-    # kernels of this library per step: the parameter kernel, then one launch per
-    # order present among the uniform rows, plus the non-uniform tiles' kernel
+    # kernels of this library per step: the parameter kernel (none when every row
+    # is a warp-segment row of the shared-memory ring kernel, which forms its
+    # own), then one launch per order present among the uniform rows, plus the
+    # non-uniform tiles' kernel
     uniform_orders = {int(o) for r, o in enumerate(w.order)} if info.n_uniform_rows else set()
-    launches_per_step = 1 + len(uniform_orders) + (1 if info.n_tiles_general else 0)
+    lens = np.diff(np.asarray(w.row_offset))
+    all_seg = (info.n_uniform_rows == w.n_rows and bool(np.all(lens >= 512))
+               and bool(np.all(lens % 4 == 0)) and bool(np.all(np.asarray(w.row_offset) % 4 == 0)))
+
+    def launches_per_step(t):
+        own = all_seg and t["uniform_kernel_f32"] == 1 and t["seg_variant_f32"] == 2
+        return (0 if own else 1) + len(uniform_orders) + (1 if info.n_tiles_general else 0)
 
     def tensors(dtype):
         q = torch.tensor(np.asarray(w.q0), dtype=dtype, device=dev)
@@ -329,7 +337,7 @@ def main():
     # flushed steps each) before the timed run.
     if not args.tuning and info.n_uniform_rows == w.n_rows:
         base = plan.tuning()
-        cands = [None] + [(v, g) for v in (0, 1) for g in (3, 4, 6, 8)]
+        cands = [None] + [(v, g) for v in (0, 1, 2) for g in (3, 4, 6, 8)]
         best, best_ms = None, float("inf")
         for c in cands:
             t = plan.tuning()
@@ -432,7 +440,7 @@ def main():
                              "per-step CUDA-event intervals",
                        "parallelism": "dp%d (independent disks per GPU)" % world,
                        "tuning": tuning},
-            "gpu_launches": int(args.steps * launches_per_step),
+            "gpu_launches": int(args.steps * launches_per_step(tuning)),
             "roofline": {"bound": "hbm", "kernel": kernel_key,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,

@@ -63,12 +63,30 @@ StepArgs base_args(const Plan *p, const void *q_in, void *q_out)
     return a;
 }
 
-ram_status run(const Plan *p, ram_dtype dt, const StepArgs &a, void *stream)
+// Every row of the plan is an FP32 warp-segment row and this launch runs them with
+// the shared-memory ring kernel (which needs 16-byte aligned arrays), which forms
+// the shift parameters itself: no parameter kernel is needed.
+bool rows_form_params(const Plan &p, ram_dtype dt, const StepArgs &a)
+{
+    if (dt != RAM_F32 || p.uniform_kernel[0] != 1 || p.seg_variant != 2) return false;
+    for (const void *ptr : {a.q_in, static_cast<const void *>(a.q_out), a.dv})
+        if ((uintptr_t)ptr % 16) return false;
+    size_t seg = 0;
+    for (int o = 2; o <= 4; ++o) seg += p.rows_seg_h[0][o].size();
+    return seg == (size_t)p.n_rows;
+}
+
+ram_status run(const Plan *p, ram_dtype dt, const StepArgs &a0, void *stream)
 {
     DeviceGuard g(p->device);
     if (!g.ok) return RAM_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_params(*p, dt, a, s);
+    StepArgs a = a0;
+    cudaError_t e = cudaSuccess;
+    if (rows_form_params(*p, dt, a))
+        a.row_phase = 1;
+    else
+        e = launch_params(*p, dt, a, s);
     if (e == cudaSuccess) e = launch_uniform(*p, dt, a, s);
     if (e == cudaSuccess) e = launch_general(*p, dt, a, s);
     if (e == cudaErrorNotSupported) return RAM_ERR_UNSUPPORTED;

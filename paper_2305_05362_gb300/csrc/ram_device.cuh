@@ -261,6 +261,128 @@ __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo 
     return xi;
 }
 
+// ---- two-float arithmetic for the shift of FP32 rows ----
+// A value is carried as an unevaluated sum h + l of two floats (about 48
+// significant bits).  The products use the error-free transformations of
+// floating-point arithmetic: the exact product of two floats is p + e with
+// p = fl(a b) and e = fma(a, b, -p), and for |a| >= |b| the exact sum is
+// s + (b - (s - a)) with s = fl(a + b) (Dekker's fast two-sum).  All of it runs
+// on the FP32 and integer pipes: an FP64 instruction costs a warp tens of cycles
+// on this part, and every CTA of a row kernel would pay that on its critical
+// path.
+struct TwoFloat {
+    float h, l;
+};
+
+__device__ __forceinline__ TwoFloat two_mul(TwoFloat a, TwoFloat b)
+{
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    const float s = p + e;
+    return {s, e - (s - p)};
+}
+
+// x as h + l from its bits (no FP64 instruction): h holds the leading 24 bits of
+// the significand, l the next 29 rounded to 24.  False for a non-finite x or
+// |x| >= 2^127; |x| < 2^-100 gives zero.
+__device__ __forceinline__ bool split_f64(double x, TwoFloat &out)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(u >> 32);
+    const int E = (int)((hi32 >> 20) & 0x7FFu) - 1023;
+    out.h = 0.0f;
+    out.l = 0.0f;
+    if (E == 1024 || E > 126) return false;
+    if (E < -100) return true;
+    const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned sign = hi32 & 0x80000000u;
+    out.h = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | ((unsigned)(M >> 29) & 0x7FFFFFu));
+    // the low 29 bits are worth R 2^(E - 52) = (R 2^-29) 2^(E - 23), E - 23 in [-123, 103]
+    const float lo = __uint2float_rn((unsigned)(M & 0x1FFFFFFFu)) * 0x1p-29f *
+                     __uint_as_float((unsigned)(E - 23 + 127) << 23);
+    out.l = sign ? -lo : lo;
+    return true;
+}
+
+// The shift parameters of one FP32 uniform row (S0 on a uniform mesh, Sec. 3.2.1),
+// computed in two-float arithmetic: sig = s N / L, with s = v0 dt (step), the
+// given shift, or zero (residual alone), is split into K = floor(sig) mod N
+// whole cells and the fraction f, and xi = 1 - f gives the coefficients of the
+// left partial integral (partial_coeffs); cf = dt N / (L nsub).  The same
+// quantities as shift_params to about 2^-46 relative in sig, which the FP32
+// cells do not resolve.  A non-finite shift, or one of 2^40 cells or more, is
+// flagged (by `lead`) and replaced by zero.  The phase is not touched.
+__device__ __forceinline__ void shift_params_two_float(const StepArgs &a, const RowInfo &row,
+                                                       int r, bool lead, RowParams<float> &P)
+{
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    const double s_in = a.mode == MODE_SHIFT ? a.shift[r] : (a.mode == MODE_STEP ? a.v0[r] : 0.0);
+    const int ns_in = has_dv ? (a.nsub ? a.nsub[r] : 1) : 0;
+    const int N = row.n;
+    P.cell_off = row.cell_off;
+    P.n = N;
+    P.sfix = 0ull;
+    TwoFloat cpl, dtc = {0.0f, 0.0f}, sig = {0.0f, 0.0f};
+    split_f64(row.cells_per_length, cpl);
+    bool fin = true;
+    if (a.mode != MODE_SHIFT) {
+        TwoFloat dt;
+        fin = split_f64(a.dt, dt);
+        dtc = two_mul(dt, cpl);
+    }
+    if (a.mode == MODE_STEP || a.mode == MODE_SHIFT) {
+        TwoFloat sv;
+        fin = split_f64(s_in, sv) && fin;
+        sig = two_mul(sv, a.mode == MODE_STEP ? dtc : cpl);
+    }
+    if (!fin || !(fabsf(sig.h) < 0x1p40f)) {
+        if (lead) atomicOr(a.err, ERR_NONFINITE);
+        sig.h = sig.l = 0.0f;
+    }
+    // floor(h + l) = floor(h) + floor(c), c = (h - floor(h)) + l: h - floor(h) is
+    // exact, and c lies in (-1, 2)
+    const float fh = floorf(sig.h);
+    const float c = (sig.h - fh) + sig.l;
+    float fc = floorf(c);
+    float f = c - fc;
+    if (f >= 1.0f) {  // c just below an integer
+        f = 0.0f;
+        fc += 1.0f;
+    }
+    int K;
+    if (fabsf(fh) < 0x1p24f) {
+        K = ((int)fh + (int)fc) % N;
+    } else {
+        K = (int)(((long long)fh + (long long)fc) % (long long)N);
+    }
+    if (K < 0) K += N;
+    P.K = K;
+    P.whole = (f == 0.0f);
+    partial_coeffs<float>(row.order, 1.0f - f, P.c);
+    int nsub = 0;
+    P.cf = 0.0f;
+    if (has_dv) {
+        nsub = ns_in;
+        if (nsub < 1 || nsub > RAM_MAX_NSUB) {
+            if (lead) atomicOr(a.err, ERR_NSUB);
+            nsub = nsub < 1 ? 1 : RAM_MAX_NSUB;
+        }
+        P.cf = (dtc.h + dtc.l) / (float)nsub;
+    }
+    P.nsub = nsub;
+}
+
+// The phase update of shift_params on its own (MODE_STEP with a phase array):
+// phase += v0 dt (zero when not finite), reduced to [0, L), in FP64.
+__device__ __forceinline__ void advance_phase(const StepArgs &a, const RowInfo &row, int r)
+{
+    if (a.mode != MODE_STEP || a.phase == nullptr) return;
+    double sft = __dmul_rn(a.v0[r], a.dt);
+    if (!isfinite(sft)) sft = 0.0;
+    a.phase[r] = reduce_mod_rcp(a.phase[r] + sft, row.period, row.inv_period);
+}
+
 // Wait until the kernels this one depends on (programmatic dependent launch)
 // have finished and their writes are visible; a no-op for a normal launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

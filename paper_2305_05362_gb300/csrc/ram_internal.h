@@ -78,6 +78,7 @@ struct StepArgs {
     const double *dx64;     // widths, FP64
     const int32_t *buckets; // per-row bucket table: cell holding each bucket start
     uint32_t wait_limit = kWaitLimit;  // tries of every bounded mbarrier wait
+    int32_t row_phase = 0;  // no parameter kernel ran: the row kernels advance the phase
 };
 
 // Shift parameters of one uniform row for one launch (S0), written by the

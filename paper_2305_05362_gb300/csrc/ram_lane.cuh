@@ -9,13 +9,28 @@
 
 namespace ram {
 
+// 1/x from the hardware reciprocal approximation (rcp.approx: relative error
+// about 2^-23; subnormal results flush to zero)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// a / b for the slope ratios of the uniform-row kernels: FP32 multiplies by the
+// approximate reciprocal (one instruction more than the product; the ratios'
+// denominators are sums of cell differences, far inside the FP32 range)
+__device__ __forceinline__ float lane_div(float a, float b) { return a * rcp_approx(b); }
+__device__ __forceinline__ double lane_div(double a, double b) { return a / b; }
+
 template <typename T>
 __device__ __forceinline__ T half_vl_relu(T dl, T dr)
 {
     // the same half slope without a select (FP32 rows): max(dl dr, 0) /
     // (dl + dr + tiny).  The tiny term only matters where |dl + dr| < 1e-30, and
     // there dl dr is either <= 0 or below the FP32 range (zero)
-    return Num<T>::div(fmax(dl * dr, T(0)), dl + dr + T(1e-30));
+    return lane_div(fmax(dl * dr, T(0)), dl + dr + T(1e-30));
 }
 
 template <typename T>
@@ -23,7 +38,7 @@ __device__ __forceinline__ T half_vl(T dl, T dr)
 {
     // half of the van Leer slope: dl dr / (dl + dr) when dl dr > 0, else 0
     const T p = dl * dr;
-    return p > T(0) ? Num<T>::div(p, dl + dr) : T(0);
+    return p > T(0) ? lane_div(p, dl + dr) : T(0);
 }
 
 // Q' for V consecutive output cells.  q[0..V+4] holds source cells p0-2..p0+V+2
@@ -137,6 +152,58 @@ __device__ __forceinline__ void residual_group(const T (&z)[V + 4], const T (&v)
     }
 #pragma unroll
     for (int k = 0; k < V; ++k) out[k] = z[k + 2] - (F[k + 1] - F[k]);
+}
+
+// One residual sub-step of a warp whose lanes hold V consecutive cells each
+// (lane l cells l V .. l V + V - 1 of the warp's range), FP32.  c[k] = dv cf is
+// the Courant number of the lane's face k (the left node of its cell k).  Every
+// lane forms the half slopes of its own cells and the fluxes of its own faces;
+// the neighbour cells and slope on the left and the flux on the right come from
+// the adjacent lanes by shuffles, so no slope or flux is formed twice.  The
+// flux is the one of residual_group; lanes 0 and 31 take their outer
+// neighbours from the other end of the warp, which spoils the outermost two
+// cells of the warp's range per van Leer sub-step (one per donor sub-step):
+// the caller keeps them as halo.
+template <int V, bool VL>
+__device__ __forceinline__ void residual_warp(float (&cur)[V], const float (&c)[V])
+{
+    const unsigned full = 0xffffffffu;
+    const float zl = __shfl_up_sync(full, cur[V - 1], 1);
+    float F[V];
+    if (VL) {
+        const float zr = __shfl_down_sync(full, cur[0], 1);
+        float d[V + 1];  // d[i] = z_i - z_{i-1}, i = 0..V
+        d[0] = cur[0] - zl;
+#pragma unroll
+        for (int i = 1; i < V; ++i) d[i] = cur[i] - cur[i - 1];
+        d[V] = zr - cur[V - 1];
+        float h[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) h[i] = half_vl_relu(d[i], d[i + 1]);
+        const float hl = __shfl_up_sync(full, h[V - 1], 1);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const float ap = fmaxf(c[k], 0.0f);
+            const float am = c[k] - ap;
+            const float zk1 = k ? cur[k - 1] : zl;
+            const float hk1 = k ? h[k - 1] : hl;
+            const float f = fmaf(ap, zk1, am * cur[k]);
+            const float wp = fmaf(-ap, ap, ap);   // c+ (1 - c+)
+            const float wm = fmaf(-am, am, -am);  // -c- (1 + c-)
+            F[k] = fmaf(wp, hk1, fmaf(wm, h[k], f));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const float ap = fmaxf(c[k], 0.0f);
+            const float am = c[k] - ap;
+            F[k] = fmaf(ap, k ? cur[k - 1] : zl, am * cur[k]);
+        }
+    }
+    const float Fr = __shfl_down_sync(full, F[0], 1);
+#pragma unroll
+    for (int k = 0; k < V - 1; ++k) cur[k] = cur[k] - (F[k + 1] - F[k]);
+    cur[V - 1] = cur[V - 1] - (Fr - F[V - 1]);
 }
 
 template <typename T>

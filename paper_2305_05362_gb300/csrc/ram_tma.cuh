@@ -81,6 +81,23 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
                  : "memory");
 }
 
+// The same copy to a shared-memory address given as a 32-bit shared-window offset.
+__device__ __forceinline__ void cp_async16_s(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// 16-byte shared-memory load from a 32-bit shared-window offset (16-byte aligned).
+__device__ __forceinline__ float4 lds128(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void cp_async_commit()
 {
     asm volatile("cp.async.commit_group;" ::: "memory");

@@ -60,7 +60,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     bool sv = false;
     for (int i = 0; i < kStreamVCount; ++i) sv |= t->stream_cells_per_lane_f32 == kStreamVCandidates[i];
     if (!sv) return RAM_ERR_ARG;
-    if (t->seg_variant_f32 != 0 && t->seg_variant_f32 != 1) return RAM_ERR_ARG;
+    if (t->seg_variant_f32 < 0 || t->seg_variant_f32 > 2) return RAM_ERR_ARG;
     if (t->seg_warps < 3 || t->seg_warps > 8) return RAM_ERR_ARG;
     if (t->rows_ctas_per_sm_f32 < 1 || t->rows_ctas_per_sm_f32 > 4 || t->rows_ctas_per_sm_f64 != 1)
         return RAM_ERR_ARG;
@@ -125,7 +125,7 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
         int best_sv = p->stream_v, best_gv = p->seg_variant, best_gw = p->seg_warps;
         float best = 3.4e38f;
         if (any_seg)
-            for (int gv = 0; gv <= (d == 0 ? 1 : 0) && st == RAM_OK; ++gv)
+            for (int gv = 0; gv <= (d == 0 ? 2 : 0) && st == RAM_OK; ++gv)
                 for (int gw : {3, 4, 6, 8}) {
                     if (st != RAM_OK) break;
                     p->uniform_kernel[d] = 1;

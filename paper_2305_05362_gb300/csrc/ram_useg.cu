@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "ram_lane.cuh"
+#include "ram_tma.cuh"
 
 namespace ram {
 namespace {
@@ -179,19 +180,29 @@ __device__ __forceinline__ void seg_step(const RowParams<T> &P, const SegRow<T> 
                 v[c * VEC + 1] = (T)d2.y;
             }
         }
-        v[V] = __shfl_down_sync(0xffffffffu, v[0], 1);
         const T cf = P.cf;
-        for (int sub = 0; sub < nsub; ++sub) {
-            T z[V + 4];
-            z[0] = __shfl_up_sync(0xffffffffu, cur[V - 2], 1);
-            z[1] = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+        if constexpr (sizeof(T) == 4) {
+            // the Courant numbers of the lane's faces are the same in every
+            // sub-step: formed (and checked against 1) once per segment
+            float c[V];
+            float cm = 0.0f;
 #pragma unroll
-            for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
-            z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
-            z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
-            if (sizeof(T) == 4) {
-                residual_group<T, V>(z, v, cf, vl, cmax, cur);
-            } else {
+            for (int k = 0; k < V; ++k) {
+                c[k] = v[k] * cf;
+                cm = fmaxf(cm, fabsf(c[k]));
+            }
+            cmax = fmaxf(cmax, cm);
+            for (int sub = 0; sub < nsub; ++sub) residual_warp<V, VL>(cur, c);
+        } else {
+            v[V] = __shfl_down_sync(0xffffffffu, v[0], 1);
+            for (int sub = 0; sub < nsub; ++sub) {
+                T z[V + 4];
+                z[0] = __shfl_up_sync(0xffffffffu, cur[V - 2], 1);
+                z[1] = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+#pragma unroll
+                for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
+                z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
+                z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
                 bool bad = false;
                 residual_group_cs<T, V>(z, v, cf, vl, bad, cur);
                 if (bad) cmax = T(2);
@@ -239,6 +250,79 @@ __global__ void __launch_bounds__(256, V * sizeof(T) <= 32 ? 3 : 2)
     for (int seg = warp; seg < S.nseg; seg += nwarps)
         seg_step<T, ORDER, V, LIM, VL>(P, S, seg, lane, cmax);
     if (cmax > T(1)) atomicOr(a.err, ERR_CFL);
+}
+
+// One FP32 warp segment from its raw window and dv vectors (in registers): the
+// remap of the lane's V cells (its source cells start at w[off + 2]), the
+// residual sub-steps with shuffled neighbours, and the store of the segment's
+// interior [H4, H4 + stride) (whole vectors; the cells past N belong to no
+// segment).  Shared by the register-prefetch and shared-memory-ring kernels.
+template <int ORDER, int V, bool LIM, bool VL>
+__device__ __forceinline__ void seg_compute_f32(const RowParams<float> &P, int N, int nsub,
+                                                int H4, int stride, int off, bool use_dv,
+                                                int seg, int lane,
+                                                const float4 (&xw)[(V + 12) / 4],
+                                                const float4 (&xv)[V / 4], float *qout,
+                                                float &cmax)
+{
+    constexpr int VEC = 4, NW = V + 12;
+    const int out0 = seg * stride;
+    const int m0 = out0 - H4 + lane * V;
+    float w[NW];
+#pragma unroll
+    for (int c = 0; c < NW / VEC; ++c) {
+        w[4 * c] = xw[c].x;
+        w[4 * c + 1] = xw[c].y;
+        w[4 * c + 2] = xw[c].z;
+        w[4 * c + 3] = xw[c].w;
+    }
+    float q[V + 5];
+    switch (off) {
+    case 0:
+#pragma unroll
+        for (int j = 0; j < V + 5; ++j) q[j] = w[j + 2];
+        break;
+    case 1:
+#pragma unroll
+        for (int j = 0; j < V + 5; ++j) q[j] = w[j + 3];
+        break;
+    case 2:
+#pragma unroll
+        for (int j = 0; j < V + 5; ++j) q[j] = w[j + 4];
+        break;
+    default:
+#pragma unroll
+        for (int j = 0; j < V + 5; ++j) q[j] = w[j + 5];
+        break;
+    }
+    float cur[V];
+    remap_group<float, ORDER, V>(q, P, LIM, cur);
+    if (use_dv) {
+        float v[V];
+#pragma unroll
+        for (int c = 0; c < V / VEC; ++c) {
+            v[4 * c] = xv[c].x;
+            v[4 * c + 1] = xv[c].y;
+            v[4 * c + 2] = xv[c].z;
+            v[4 * c + 3] = xv[c].w;
+        }
+        float cm = 0.0f;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            v[k] *= P.cf;  // the faces' Courant numbers, the same in every sub-step
+            cm = fmaxf(cm, fabsf(v[k]));
+        }
+        cmax = fmaxf(cmax, cm);
+        for (int sub = 0; sub < nsub; ++sub) residual_warp<V, VL>(cur, v);
+    }
+    const int li0 = lane * V;
+#pragma unroll
+    for (int c = 0; c < V / VEC; ++c) {
+        const int li = li0 + c * VEC;
+        if (li >= H4 && li < H4 + stride && m0 + c * VEC < N)
+            *reinterpret_cast<float4 *>(qout + m0 + c * VEC) =
+                make_float4(cur[4 * c], cur[4 * c + 1], cur[4 * c + 2], cur[4 * c + 3]);
+    }
 }
 
 // The same step with the loads of a warp's next segment in flight while it
@@ -303,66 +387,8 @@ __global__ void __launch_bounds__(256, 2)
         }
     };
     auto compute = [&](int seg, const Raw &x) {
-        const int out0 = seg * stride;
-        const int m0 = out0 - H4 + lane * V;
-        float w[NW];
-#pragma unroll
-        for (int c = 0; c < NW / VEC; ++c) {
-            w[4 * c] = x.w[c].x;
-            w[4 * c + 1] = x.w[c].y;
-            w[4 * c + 2] = x.w[c].z;
-            w[4 * c + 3] = x.w[c].w;
-        }
-        float q[V + 5];
-        switch (off) {
-        case 0:
-#pragma unroll
-            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 2];
-            break;
-        case 1:
-#pragma unroll
-            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 3];
-            break;
-        case 2:
-#pragma unroll
-            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 4];
-            break;
-        default:
-#pragma unroll
-            for (int j = 0; j < V + 5; ++j) q[j] = w[j + 5];
-            break;
-        }
-        float cur[V];
-        remap_group<float, ORDER, V>(q, P, LIM, cur);
-        if (use_dv) {
-            float v[V + 1];
-#pragma unroll
-            for (int c = 0; c < V / VEC; ++c) {
-                v[4 * c] = x.v[c].x;
-                v[4 * c + 1] = x.v[c].y;
-                v[4 * c + 2] = x.v[c].z;
-                v[4 * c + 3] = x.v[c].w;
-            }
-            v[V] = __shfl_down_sync(0xffffffffu, v[0], 1);
-            for (int sub = 0; sub < nsub; ++sub) {
-                float z[V + 4];
-                z[0] = __shfl_up_sync(0xffffffffu, cur[V - 2], 1);
-                z[1] = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
-#pragma unroll
-                for (int k = 0; k < V; ++k) z[k + 2] = cur[k];
-                z[V + 2] = __shfl_down_sync(0xffffffffu, cur[0], 1);
-                z[V + 3] = __shfl_down_sync(0xffffffffu, cur[1], 1);
-                residual_group<float, V>(z, v, P.cf, VL, cmax, cur);
-            }
-        }
-        const int li0 = lane * V;
-#pragma unroll
-        for (int c = 0; c < V / VEC; ++c) {
-            const int li = li0 + c * VEC;
-            if (li >= H4 && li < H4 + stride && m0 + c * VEC < N)
-                *reinterpret_cast<float4 *>(qout + m0 + c * VEC) =
-                    make_float4(cur[4 * c], cur[4 * c + 1], cur[4 * c + 2], cur[4 * c + 3]);
-        }
+        seg_compute_f32<ORDER, V, LIM, VL>(P, N, nsub, H4, stride, off, use_dv, seg, lane, x.w,
+                                           x.v, qout, cmax);
     };
 
     Raw ra, rb;
@@ -375,6 +401,130 @@ __global__ void __launch_bounds__(256, 2)
         if (s2 < nseg) load(s2, ra);
         if (s1 < nseg) compute(s1, rb);
     }
+    if (cmax > 1.0f) atomicOr(a.err, ERR_CFL);
+}
+
+// Shared-memory layout of the ring kernel, per warp: S stages, each the warp
+// segment's source window (32 V + 12 cells from a 16-byte aligned start)
+// followed by its dv (32 V cells).
+template <int V>
+struct RingLayout {
+    static constexpr int WQ = 32 * V + 12;
+    static constexpr int WV = 32 * V;
+    static constexpr int S = V == 8 ? 4 : 3;
+    static constexpr int stage_floats = WQ + WV;
+    static constexpr int warp_bytes = S * stage_floats * 4;
+    static_assert((stage_floats * 4) % 16 == 0, "16-byte aligned stages");
+};
+
+// The same step with each warp's segments staged through a ring of S shared-memory
+// stages filled by asynchronous 16-byte copies (the data does not pass through
+// registers until the segment is computed), so that S segments per warp are in
+// flight.  A warp reads a stage into registers, refills it at once with the
+// copies of its segment S ahead and computes.  The row's shift parameters are
+// formed in the kernel (shift_params_two_float), so no parameter kernel runs
+// before it when every row of the step takes this kernel; the phase is then
+// advanced here too (a.row_phase).  FP32 rows of at least 32 V + 12 cells.
+template <int ORDER, int V, bool LIM, bool VL>
+__global__ void __launch_bounds__(256, V == 8 ? 3 : 2)
+    k_useg_ring(StepArgs a, const int32_t *row_ids)
+{
+    using L = RingLayout<V>;
+    constexpr int VEC = 4, NW = V + 12;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    float *ring = reinterpret_cast<float *>(smem_raw + (size_t)warp * L::warp_bytes);
+
+    const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
+    const int r = row_ids[blockIdx.x];
+    const RowInfo row = a.rows[r];  // plan data: readable before the previous kernel ends
+    pdl_wait();
+    // every warp forms the row's shift parameters itself, in two-float arithmetic
+    // (no FP64 instruction, no parameter kernel before this one)
+    RowParams<float> P;
+    shift_params_two_float(a, row, r, threadIdx.x == 0, P);
+    if (a.row_phase && threadIdx.x == 0) advance_phase(a, row, r);
+    const int N = P.n;
+    const int nsub = P.nsub;
+    const int H4 = ((nsub * (VL ? 2 : 1) + VEC - 1) / VEC) * VEC;
+    const int stride = 32 * V - 2 * H4;
+    const int nseg = (N + stride - 1) / stride;
+    const float *qin = static_cast<const float *>(a.q_in) + P.cell_off;
+    const float *dvp = has_dv ? static_cast<const float *>(a.dv) + P.cell_off : nullptr;
+    float *qout = static_cast<float *>(a.q_out) + P.cell_off;
+    const int off = ((-P.K - 1) % VEC + VEC) % VEC;
+    const bool use_dv = has_dv && nsub > 0;
+    const int nmine = warp < nseg ? (nseg - warp + nwarps - 1) / nwarps : 0;
+
+    // copies of this warp's i-th segment into stage i % S, one commit group per
+    // segment (empty past the warp's last one, so that group i is always the
+    // (i+1)-th).  The window starts at the 16-byte aligned cell wb in [0, N); a
+    // vector past the row's end comes from its start.  Lane l copies the 16-byte
+    // chunks l, l + 32, ... of the window and of the dv range.
+    const uint32_t ring_s = smem_u32(ring) + 16u * lane;
+    constexpr uint32_t kStageBytes = L::stage_floats * 4;
+    const int wshift = P.K + 1 + off + VEC;  // window start = w0 - wshift
+    const float *const qlane = qin + 4 * lane;
+    const float *const dlane = use_dv ? dvp + 4 * lane : nullptr;
+    auto issue = [=](int i) {
+        if (i < nmine) {
+            const int w0 = (warp + i * nwarps) * stride - H4;
+            const uint32_t sq = ring_s + (uint32_t)(i % L::S) * kStageBytes;
+            const int wb = wrap2(w0 - wshift, N);
+            if (wb + L::WQ <= N) {
+                const float *src = qlane + wb;
+#pragma unroll
+                for (int j = 0; j < (L::WQ / 4 + 31) / 32; ++j)
+                    if (lane + 32 * j < L::WQ / 4) cp_async16_s(sq + 512u * j, src + 128 * j);
+            } else {
+#pragma unroll
+                for (int j = 0; j < (L::WQ / 4 + 31) / 32; ++j) {
+                    const int c = lane + 32 * j;
+                    if (c < L::WQ / 4) cp_async16_s(sq + 512u * j, qin + wrap1(wb + 4 * c, N));
+                }
+            }
+            if (use_dv) {
+                const int wv = wrap2(w0, N);
+                const uint32_t sv = sq + L::WQ * 4;
+                if (wv + L::WV <= N) {
+                    const float *src = dlane + wv;
+#pragma unroll
+                    for (int j = 0; j < L::WV / 128; ++j) cp_async16_s(sv + 512u * j, src + 128 * j);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < L::WV / 128; ++j)
+                        cp_async16_s(sv + 512u * j, dvp + wrap1(wv + 4 * (lane + 32 * j), N));
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll
+    for (int i = 0; i < L::S; ++i) issue(i);
+    float cmax = 0.0f;
+    // this lane's cells in a stage: window floats lane V .., dv floats WQ + lane V ..
+    const uint32_t lds0 = smem_u32(ring) + 4u * V * lane;
+    for (int i = 0; i < nmine; ++i) {
+        // S + i groups committed; segment i's is complete once at most S - 1 remain
+        cp_async_wait<L::S - 1>();
+        __syncwarp();
+        const uint32_t sq = lds0 + (uint32_t)(i % L::S) * kStageBytes;
+        float4 xw[NW / VEC], xv[V / VEC];
+#pragma unroll
+        for (int c = 0; c < NW / VEC; ++c) xw[c] = lds128(sq + 16u * c);
+        if (use_dv) {
+#pragma unroll
+            for (int c = 0; c < V / VEC; ++c) xv[c] = lds128(sq + L::WQ * 4 + 16u * c);
+        }
+        // every lane has read the stage: refill it with the segment S ahead
+        __syncwarp();
+        issue(i + L::S);
+        seg_compute_f32<ORDER, V, LIM, VL>(P, N, nsub, H4, stride, off, use_dv,
+                                           warp + i * nwarps, lane, xw, xv, qout, cmax);
+    }
+    cp_async_wait<0>();
     if (cmax > 1.0f) atomicOr(a.err, ERR_CFL);
 }
 
@@ -408,12 +558,52 @@ cudaError_t launch_useg_pf(const StepArgs &a, cudaStream_t s, int threads, const
     return launch_pdl(k_useg_pf<ORDER, false, false>, n_rows, threads, 0, s, a, row_ids, par);
 }
 
+template <int ORDER, int V, bool LIM, bool VL>
+cudaError_t launch_ring_k(const Plan &p, const StepArgs &a, cudaStream_t s, int threads,
+                          const int32_t *row_ids, int n_rows)
+{
+    const size_t smem = (size_t)(threads / 32) * RingLayout<V>::warp_bytes;
+    static bool configured[64] = {false};
+    const int dev = p.device < 64 ? p.device : 63;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_useg_ring<ORDER, V, LIM, VL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(227 * 1024));
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    return launch_pdl(k_useg_ring<ORDER, V, LIM, VL>, n_rows, threads, smem, s, a, row_ids);
+}
+
+template <int ORDER, int V>
+cudaError_t launch_useg_ring(const Plan &p, const StepArgs &a, cudaStream_t s, int threads,
+                             const int32_t *row_ids, int n_rows)
+{
+    const bool lim = a.limiter != 0, vl = a.scheme == RAM_VANLEER;
+    if (lim && vl) return launch_ring_k<ORDER, V, true, true>(p, a, s, threads, row_ids, n_rows);
+    if (lim) return launch_ring_k<ORDER, V, true, false>(p, a, s, threads, row_ids, n_rows);
+    if (vl) return launch_ring_k<ORDER, V, false, true>(p, a, s, threads, row_ids, n_rows);
+    return launch_ring_k<ORDER, V, false, false>(p, a, s, threads, row_ids, n_rows);
+}
+
+template <int ORDER>
+cudaError_t launch_useg_f32(const Plan &p, const StepArgs &a, cudaStream_t s, int threads,
+                            const int32_t *row_ids, int n_rows, const RowParams<float> *par)
+{
+    switch (p.seg_variant) {
+    case 1: return launch_useg_pf<ORDER>(a, s, threads, row_ids, n_rows, par);
+    case 2: return launch_useg_ring<ORDER, 8>(p, a, s, threads, row_ids, n_rows);
+    default: return launch_useg_v<float, ORDER, 8>(a, s, threads, row_ids, n_rows, par);
+    }
+}
+
 }  // namespace
 
 // Rows for this kernel: the plan's warp-segment list (16-byte aligned rows of at
 // least 512 cells, so that a lane's window wraps the row at most once); 8 (FP32)
-// or 4 (FP64) cells per lane; FP32 with or without the next segment's loads in
-// flight (the plan's choice).
+// or 4 (FP64) cells per lane.  FP32 takes the plan's variant: 0 one segment in
+// flight per warp, 1 the next segment's loads in flight in registers, 2 a ring of
+// shared-memory stages per warp (with the shift parameters formed in the kernel).
 cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
                         int order, const int32_t *row_ids, int n_rows)
 {
@@ -424,14 +614,9 @@ cudaError_t launch_useg(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStre
     const RowParams<float> *pf = static_cast<const RowParams<float> *>(p.row_par);
     const RowParams<double> *pd = static_cast<const RowParams<double> *>(p.row_par);
     if (dt == RAM_F32) {
-        if (p.seg_variant) {
-            if (order == 2) return launch_useg_pf<2>(a, s, threads, row_ids, n_rows, pf);
-            if (order == 3) return launch_useg_pf<3>(a, s, threads, row_ids, n_rows, pf);
-            return launch_useg_pf<4>(a, s, threads, row_ids, n_rows, pf);
-        }
-        if (order == 2) return launch_useg_v<float, 2, 8>(a, s, threads, row_ids, n_rows, pf);
-        if (order == 3) return launch_useg_v<float, 3, 8>(a, s, threads, row_ids, n_rows, pf);
-        return launch_useg_v<float, 4, 8>(a, s, threads, row_ids, n_rows, pf);
+        if (order == 2) return launch_useg_f32<2>(p, a, s, threads, row_ids, n_rows, pf);
+        if (order == 3) return launch_useg_f32<3>(p, a, s, threads, row_ids, n_rows, pf);
+        return launch_useg_f32<4>(p, a, s, threads, row_ids, n_rows, pf);
     }
     if (order == 2) return launch_useg_v<double, 2, 4>(a, s, threads, row_ids, n_rows, pd);
     if (order == 3) return launch_useg_v<double, 3, 4>(a, s, threads, row_ids, n_rows, pd);

@@ -54,13 +54,18 @@ def test_wait_timeout_is_reported_and_context_survives(dtype):
     assert torch.equal(again, ref)
 
 
-def test_kernels_without_waits_ignore_the_limit():
-    """The warp-segment kernel has no waits: a try count of 0 changes nothing."""
-    w = wl.disk(256, 1024)
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_kernels_without_waits_ignore_the_limit(variant):
+    """The warp-segment kernels (one segment in flight, the next one's loads in
+    flight, shared-memory rings of asynchronous copies) have no waits of their
+    own: a try count of 0 changes nothing."""
+    w = wl.disk(64, 8192)
     plan = ram.Plan.from_workload(w)
     t = plan.tuning()
     t.uniform_kernel_f32 = 1
     t.uniform_kernel_f64 = 1
+    t.seg_variant_f32 = variant
+    t.seg_warps = 3
     plan.set_tuning(t)
     for dtype in ("float64", "float32"):
         q, v0, dv, ns = _inputs(w, dtype)

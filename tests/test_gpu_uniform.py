@@ -336,10 +336,11 @@ def test_both_uniform_kernels_match_oracle(dtype, scheme, nsub_max):
                                        oracle.shift_from_velocity(v0[r], dt), 3, True,
                                        dvr[r * n_phi:(r + 1) * n_phi], dt, scheme, int(nsub[r]))
                            for r in range(n_r)])
-    # kernels: 0 whole-row, 1 warp segments (FP32: without / with prefetch; 3-8
-    # warps per row CTA), 2 streaming warps (FP32; V = 4, 8)
-    for kern, sv, gw in ((0, 8, 8), (1, 0, 8), (1, 0, 3), (1, 1, 6), (1, 1, 4), (2, 4, 8),
-                         (2, 8, 8)):
+    # kernels: 0 whole-row, 1 warp segments (FP32: one segment in flight, the next
+    # one's loads in flight, shared-memory rings with the shift parameters formed
+    # in the kernel; 3-8 warps per row CTA), 2 streaming warps (FP32; V = 4, 8)
+    for kern, sv, gw in ((0, 8, 8), (1, 0, 8), (1, 0, 3), (1, 1, 6), (1, 1, 4), (1, 2, 3),
+                         (1, 2, 8), (2, 4, 8), (2, 8, 8)):
         if kern == 2 and dtype == "float64":
             continue
         t = plan.tuning()
