@@ -115,6 +115,62 @@ __device__ __forceinline__ void remap_group(const T (&q)[V + 5], const RowParams
     for (int k = 0; k < V; ++k) out[k] = (q[k + 2] - A[k]) + A[k + 1];
 }
 
+// The PPM remap of remap_group for a warp whose lanes hold V consecutive cells
+// each (FP32, lean form), with every limited slope and every left partial
+// formed once: a lane forms those of its own V source cells p0 .. p0+V-1 and
+// takes the slope of cell p0-1 from the lane on its left, and the slope of cell
+// p0+V and the partial of cell p0+V from the lane on its right.  q[0..V+4] holds
+// source cells p0-2 .. p0+V+2 (this form reads q[1..V+2]).  Lanes 0 and 31 take
+// their outer neighbours from the other end of the warp, which spoils the warp's
+// first output cell and its last two: the caller keeps them as halo.
+template <int V>
+__device__ __forceinline__ void remap_warp3(const float (&q)[V + 5], const RowParams<float> &P,
+                                            bool lim, float (&out)[V])
+{
+    if (P.whole) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = q[k + 3];
+        return;
+    }
+    const unsigned full = 0xffffffffu;
+    float dif[V + 1];  // dif[i] = Q(p0-1+i+1) - Q(p0-1+i), i = 0..V
+#pragma unroll
+    for (int i = 0; i <= V; ++i) dif[i] = q[i + 2] - q[i + 1];
+    float Dq[V + 2];   // 2 dQ of cells p0-1 .. p0+V; own cells at Dq[1..V]
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const float D = dif[j] + dif[j + 1];
+        Dq[j + 1] = lim ? minxs(D, fmaxf(4.0f * minxs(dif[j], dif[j + 1]), 0.0f)) : D;
+    }
+    Dq[0] = __shfl_up_sync(full, Dq[V], 1);
+    Dq[V + 1] = __shfl_down_sync(full, Dq[1], 1);
+    float E[V + 1];    // E[i] = Dq(p0+i) - Dq(p0+i-1)
+#pragma unroll
+    for (int i = 0; i <= V; ++i) E[i] = Dq[i + 1] - Dq[i];
+    const float xi = P.c[3], cR = P.c[1], cL = P.c[0];
+    float A[V + 1];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        // cell p0+j: right face from dif[j+1], E[j+1]; left face from dif[j], E[j]
+        const float a = fmaf(E[j + 1], -1.0f / 12.0f, 0.5f * dif[j + 1]);
+        const float b = fmaf(E[j], 1.0f / 12.0f, 0.5f * dif[j]);
+        float G;
+        if (lim) {
+            const float a2 = fmaf(E[j + 1], -1.0f / 6.0f, dif[j + 1]);  // 2a
+            const float b2 = fmaf(E[j], 1.0f / 6.0f, dif[j]);           // 2b
+            const float u = fmaxf(minxs(a, b2), 0.0f);                  // |a'|
+            const float v = fmaxf(minxs(b, a2), 0.0f);                  // |b'|
+            G = xorsign(fmaf(cR, u, -cL * v), a);
+        } else {
+            G = fmaf(cR, a, -cL * b);
+        }
+        A[j] = fmaf(xi, q[j + 2], G);
+    }
+    A[V] = __shfl_down_sync(full, A[0], 1);
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = (q[k + 2] - A[k]) + A[k + 1];
+}
+
 // One residual sub-step for V cells m0..m0+V-1.  z[0..V+3] holds Q at cells
 // m0-2..m0+V+1, v[0..V] the interface velocities at m0..m0+V (interface k is the
 // left node of cell m0+k).  The flux through interface k (Eq. 6 with the PLM

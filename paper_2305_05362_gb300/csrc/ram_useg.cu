@@ -296,7 +296,10 @@ __device__ __forceinline__ void seg_compute_f32(const RowParams<float> &P, int N
         break;
     }
     float cur[V];
-    remap_group<float, ORDER, V>(q, P, LIM, cur);
+    if constexpr (ORDER == 3)
+        remap_warp3<V>(q, P, LIM, cur);
+    else
+        remap_group<float, ORDER, V>(q, P, LIM, cur);
     if (use_dv) {
         float v[V];
 #pragma unroll
@@ -341,8 +344,14 @@ __global__ void __launch_bounds__(256, 2)
     const RowParams<float> P = pars[r];
     const int N = P.n;
     const int nsub = P.nsub;
-    const int H4 = ((nsub * (VL ? 2 : 1) + VEC - 1) / VEC) * VEC;
-    const int stride = 32 * V - 2 * H4;
+    // halo at the ends of a warp's 32 V cells, whole vectors: the residual
+    // sub-steps spoil nsub (donor) or 2 nsub (van Leer) cells at each end, and
+    // the PPM remap with shared neighbours (remap_warp3) 1 more on the left and 2
+    // on the right; H4 cells on the left, HR on the right are not stored
+    const int spoil = nsub * (VL ? 2 : 1);
+    const int H4 = ((spoil + (ORDER == 3 ? 1 : 0) + VEC - 1) / VEC) * VEC;
+    const int HR = ((spoil + (ORDER == 3 ? 2 : 0) + VEC - 1) / VEC) * VEC;
+    const int stride = 32 * V - H4 - HR;
     const int nseg = (N + stride - 1) / stride;
     const float *qin = static_cast<const float *>(a.q_in) + P.cell_off;
     const float *dvp = has_dv ? static_cast<const float *>(a.dv) + P.cell_off : nullptr;
@@ -447,8 +456,14 @@ __global__ void __launch_bounds__(256, V == 8 ? 3 : 2)
     if (a.row_phase && threadIdx.x == 0) advance_phase(a, row, r);
     const int N = P.n;
     const int nsub = P.nsub;
-    const int H4 = ((nsub * (VL ? 2 : 1) + VEC - 1) / VEC) * VEC;
-    const int stride = 32 * V - 2 * H4;
+    // halo at the ends of a warp's 32 V cells, whole vectors: the residual
+    // sub-steps spoil nsub (donor) or 2 nsub (van Leer) cells at each end, and
+    // the PPM remap with shared neighbours (remap_warp3) 1 more on the left and 2
+    // on the right; H4 cells on the left, HR on the right are not stored
+    const int spoil = nsub * (VL ? 2 : 1);
+    const int H4 = ((spoil + (ORDER == 3 ? 1 : 0) + VEC - 1) / VEC) * VEC;
+    const int HR = ((spoil + (ORDER == 3 ? 2 : 0) + VEC - 1) / VEC) * VEC;
+    const int stride = 32 * V - H4 - HR;
     const int nseg = (N + stride - 1) / stride;
     const float *qin = static_cast<const float *>(a.q_in) + P.cell_off;
     const float *dvp = has_dv ? static_cast<const float *>(a.dv) + P.cell_off : nullptr;
