@@ -54,16 +54,20 @@ def _workload(name, rank, disk=None):
         return wl.disk(n_r=8192, n_phi=16384, seed_dv=4 + rank, dtype=np.float32)
     if name == "batched":
         return wl.batched(n_rows=512, seed_len=6 + 100 * rank)
+    if name == "batched_large":
+        return wl.batched(n_rows=8192, seed_len=6 + 100 * rank)
     raise SystemExit("unknown workload %s" % name)
 
 
 def _bytes_per_cell(w, es):
     """Algorithmic bytes of one step per cell: read Q, write Q, read dv when the
-    residual step runs, read the row's own mesh (8 B fixed-point node + width)
-    for non-uniform rows."""
+    residual step runs, and read the row's own mesh (one 8-byte node per cell)
+    when the rows do not share one."""
     b = 2 * es
     if w.dv is not None:
         b += es
+    if not w.shared_mesh:
+        b += 8
     return b
 
 
@@ -219,7 +223,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="disk", choices=["disk", "disk_large", "batched"])
+    ap.add_argument("--workload", default="disk", choices=["disk", "disk_large", "batched", "batched_large"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=50)

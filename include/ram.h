@@ -200,7 +200,7 @@ ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *tuning);
  * for FP32 the streaming-warp kernel with 4 or 8 cells per lane, and the
  * persistent whole-row kernel with (cells per thread, CTAs per SM) in
  * {5,7,9,11,15} x {2,3,4} as the register budget allows; tile cells
- * {256,512,1024,2048} x threads {128,256} of the tiled kernels.  Host
+ * {256,512,1024,2048} x threads {128,256,512} of the tiled kernels.  Host
  * synchronous; overwrites q_out. */
 ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
                              const double *v0, double dt, const void *dv_iface,

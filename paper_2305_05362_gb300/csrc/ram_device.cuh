@@ -393,10 +393,29 @@ __device__ __forceinline__ void pdl_trigger()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// i reduced to [0, n).  The tiled kernels call it per cell with i within one
+// period of the row, where one compare-and-add does it; a 64-bit remainder (a
+// long software sequence) is left for the far cases (rows shorter than a halo).
 __device__ __forceinline__ int wrap_index(int64_t i, int n)
 {
+    if (i >= -(int64_t)n && i < 2 * (int64_t)n) {
+        int x = (int)i;
+        if (x < 0)
+            x += n;
+        else if (x >= n)
+            x -= n;
+        return x;
+    }
     int64_t k = i % n;
     return (int)(k < 0 ? k + n : k);
+}
+
+// x >= 0 reduced to [0, n), with the same fast path.
+__device__ __forceinline__ int wrap_pos(int x, int n)
+{
+    if (x < n) return x;
+    if (x < 2 * n) return x - n;
+    return x % n;
 }
 
 }  // namespace ram

@@ -302,7 +302,7 @@ __host__ __device__ inline GLayout general_layout(int wcap, int qcap)
 }
 
 template <typename T, int ORDER>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     k_general(StepArgs a, int wcap, int qcap, const RowParams<T> *pars)
 {
     using AC = Acc<T>;
@@ -377,11 +377,11 @@ __global__ void __launch_bounds__(256)
     const uint64_t xbase = s_xbase;
     const int wb = wrap_index((int64_t)plo - kHR, N);  // cell of slot 0
     for (int w = tid; w < W; w += nth) {
-        const int c = (wb + w) % N;
+        const int c = wrap_pos(wb + w, N);
         sQ[w] = qin[c];
         sDX[w] = DX[c];
     }
-    for (int w = kHR + tid; w <= W - kHR; w += nth) sY[w] = X[(wb + w) % N] - xbase;
+    for (int w = kHR + tid; w <= W - kHR; w += nth) sY[w] = X[wrap_pos(wb + w, N)] - xbase;
     // output cells a-H .. a+T+H (cyclic): node positions, widths, dv
     for (int j = tid; j <= nq; j += nth) {
         const int e = wrap_index((int64_t)tile.start - H + j, N);
@@ -515,7 +515,9 @@ cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s)
     StepArgs a = a0;
     a.tiles = p.tiles_general[ORDER];
     a.n_tiles = (int)th.size();
-    return launch_pdl(k_general<T, ORDER>, (int)th.size(), 256, smem, s, a, wcap, qcap,
+    // the plan's threads per CTA (every phase of a tile strides over its cells)
+    const int threads = p.threads < 512 ? p.threads : 512;
+    return launch_pdl(k_general<T, ORDER>, (int)th.size(), threads, smem, s, a, wcap, qcap,
                       static_cast<const RowParams<T> *>(p.row_par));
 }
 

@@ -192,34 +192,40 @@ ram_status build_tiles(Plan &p)
         std::vector<double> w2(2 * (size_t)n);
         for (int i = 0; i < n; ++i) w2[i] = w2[i + n] = x[i + 1] - x[i];
         const int nt = (n + tg - 1) / tg;
+        // the longest physical extent of a tile's output cells with their halo,
+        // [a - halo, b + halo) (cyclic), bounds the source cells of every tile
+        double len_max = 0.0;
         for (int t = 0; t < nt; ++t) {
             const int a = (int)((int64_t)n * t / nt);
             const int b = (int)((int64_t)n * (t + 1) / nt);
-            Tile tl{r, a, b - a, 0};
-            // physical length of the output cells [a - halo, b + halo) (cyclic)
             const int span = (b - a) + 2 * halo_res;
-            double len = 0.0;
             const int first = ((a - halo_res) % n + n) % n;
+            double len = 0.0;
             for (int k = 0; k < span; ++k) len += w2[(first + k) % (2 * n)];
-            // most source cells an interval of that length can touch: for every
-            // start s, cells s..e-1 fit strictly inside it; it also touches cell e
-            // and the cell s-1 it may start in
-            int best = 0;
-            double acc = 0.0;
-            int e = 0;
-            for (int st = 0; st < n; ++st) {
-                if (e < st) {
-                    e = st;
-                    acc = 0.0;
-                }
-                while (e < st + n && acc + w2[e] < len) acc += w2[e++];
-                best = std::max(best, e - st + 2);
-                if (e > st) acc -= w2[st];
+            len_max = std::max(len_max, len);
+        }
+        // most source cells an interval of that length can touch (one pass over the
+        // row): for every start s, cells s..e-1 fit strictly inside it; it also
+        // touches cell e and the cell s-1 it may start in
+        int best = 0;
+        double acc = 0.0;
+        int e = 0;
+        for (int st = 0; st < n; ++st) {
+            if (e < st) {
+                e = st;
+                acc = 0.0;
             }
-            best = std::min(best, n + 1);
-            tl.window = best + 2 * 2 + 2;  // reconstruction halo (2 per side) + slack
-            p.window_max = std::max(p.window_max, tl.window);
-            p.tiles_general_h[ri.order].push_back(tl);
+            while (e < st + n && acc + w2[e] < len_max) acc += w2[e++];
+            best = std::max(best, e - st + 2);
+            if (e > st) acc -= w2[st];
+        }
+        best = std::min(best, n + 1);
+        const int window = best + 2 * 2 + 2;  // reconstruction halo (2 per side) + slack
+        p.window_max = std::max(p.window_max, window);
+        for (int t = 0; t < nt; ++t) {
+            const int a = (int)((int64_t)n * t / nt);
+            const int b = (int)((int64_t)n * (t + 1) / nt);
+            p.tiles_general_h[ri.order].push_back(Tile{r, a, b - a, window});
         }
     }
     for (int o = 2; o <= 4; ++o) {

@@ -179,7 +179,7 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
     }
     if (any_tiles && st == RAM_OK) {
         const int tcs[] = {256, 512, 1024, 2048};
-        const int ths[] = {128, 256};
+        const int ths[] = {128, 256, 512};
         int best_tc = p->tile_cells, best_th = p->threads;
         float best = 3.4e38f;
         for (int tc : tcs)

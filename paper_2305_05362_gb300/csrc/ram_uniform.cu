@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(1024)
             sQ[w] = qin[c];
         }
     } else {
-        for (int w = tid; w < Wn; w += nth) sQ[w] = qin[(w0 + w) % N];
+        for (int w = tid; w < Wn; w += nth) sQ[w] = qin[wrap_pos(w0 + w, N)];
     }
     __syncthreads();
 
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(1024)
                 sV[j] = dv[c];
             }
         } else {
-            for (int j = tid; j <= nq; j += nth) sV[j] = dv[(v0i + j) % N];
+            for (int j = tid; j <= nq; j += nth) sV[j] = dv[wrap_pos(v0i + j, N)];
         }
         const T cf = P.cf;  // Courant number per unit dv
         const bool vl = (a.scheme == RAM_VANLEER);
