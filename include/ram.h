@@ -183,9 +183,15 @@ typedef struct {
     int32_t rows_ctas_per_sm_f64;       /* whole-row kernel, FP64: 1 */
     int32_t stream_cells_per_lane_f32;  /* streaming-warp kernel, FP32: 4 or 8 cells per
                                            lane and segment (8 needs rows >= 520 cells) */
-    int32_t seg_variant_f32;            /* warp-segment kernel, FP32: 1 = the loads of a
-                                           warp's next segment in flight while it computes */
-    int32_t seg_warps;                  /* warp-segment kernel: warps per row CTA, 3..8 */
+    int32_t seg_variant_f32;            /* warp-segment kernel, FP32: 0 = one segment in
+                                           flight per warp, 1 = the loads of a warp's next
+                                           segment in flight while it computes, 2 = a ring
+                                           of 4 shared-memory stages per warp, the row's
+                                           shift parameters formed in the kernel (no
+                                           parameter kernel when every row takes it;
+                                           the default) */
+    int32_t seg_warps;                  /* warp-segment kernel: warps per row CTA, 3..8
+                                           (default 3) */
 } ram_tuning;
 
 ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out);

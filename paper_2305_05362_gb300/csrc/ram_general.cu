@@ -349,39 +349,34 @@ __global__ void __launch_bounds__(512)
     const int nq = T_out + 2 * H;
     const bool whole = tile.window == 0;
 
-    // ---- the source window ----
-    if (tid == 0) {
-        int plo, W;
-        uint64_t xbase;
-        if (whole) {
-            plo = 0;
-            W = N + 2 * kHR;
-            xbase = 0;
-        } else {
-            const int elo = wrap_index((int64_t)tile.start - H, N);
-            const int ehi = wrap_index((int64_t)tile.start + T_out + H, N);
-            plo = locate_row(X, N, bt, row.bucket_bits, X[elo] - S);
-            const int phi = locate_row(X, N, bt, row.bucket_bits, X[ehi] - S);
+    // ---- the source window, and the output side's nodes, widths and dv ----
+    // Lanes 0 and 1 locate the source cells of the tile's two outer edges at the
+    // same time (each a short chain of dependent loads: the node, its bucket, a
+    // walk); the other threads meanwhile load the output side, which does not
+    // depend on the window.
+    if (tid < 32) {
+        int plo = 0, W = N + 2 * kHR;
+        uint64_t xbase = 0;
+        if (!whole) {
+            int p = 0;
+            if (tid < 2) {
+                const int e = tid == 0 ? wrap_index((int64_t)tile.start - H, N)
+                                       : wrap_index((int64_t)tile.start + T_out + H, N);
+                p = locate_row(X, N, bt, row.bucket_bits, X[e] - S);
+            }
+            const int phi = __shfl_sync(0xffffffffu, p, 1);
+            plo = p;
             W = (phi - plo + N) % N + 1 + 2 * kHR;
-            xbase = X[plo];
+            if (tid == 0) xbase = X[plo];
         }
-        s_plo = plo;
-        s_W = W;
-        s_xbase = xbase;
-        s_bad = (W > wcap);
-        if (s_bad) atomicOr(a.err, ERR_WINDOW);
+        if (tid == 0) {
+            s_plo = plo;
+            s_W = W;
+            s_xbase = xbase;
+            s_bad = (W > wcap);
+            if (s_bad) atomicOr(a.err, ERR_WINDOW);
+        }
     }
-    __syncthreads();
-    if (s_bad) return;
-    const int plo = s_plo, W = s_W;
-    const uint64_t xbase = s_xbase;
-    const int wb = wrap_index((int64_t)plo - kHR, N);  // cell of slot 0
-    for (int w = tid; w < W; w += nth) {
-        const int c = wrap_pos(wb + w, N);
-        sQ[w] = qin[c];
-        sDX[w] = DX[c];
-    }
-    for (int w = kHR + tid; w <= W - kHR; w += nth) sY[w] = X[wrap_pos(wb + w, N)] - xbase;
     // output cells a-H .. a+T+H (cyclic): node positions, widths, dv
     for (int j = tid; j <= nq; j += nth) {
         const int e = wrap_index((int64_t)tile.start - H + j, N);
@@ -393,6 +388,17 @@ __global__ void __launch_bounds__(512)
                        : nullptr;
     if (nsub > 0)
         for (int j = tid; j <= nq; j += nth) sV[j] = dvp[wrap_index((int64_t)tile.start - H + j, N)];
+    __syncthreads();
+    if (s_bad) return;
+    const int plo = s_plo, W = s_W;
+    const uint64_t xbase = s_xbase;
+    const int wb = wrap_index((int64_t)plo - kHR, N);  // cell of slot 0
+    for (int w = tid; w < W; w += nth) {
+        const int c = wrap_pos(wb + w, N);
+        sQ[w] = qin[c];
+        sDX[w] = DX[c];
+    }
+    for (int w = kHR + tid; w <= W - kHR; w += nth) sY[w] = X[wrap_pos(wb + w, N)] - xbase;
     __syncthreads();
 
     // ---- prefix sum of the window masses (Eq. 18's whole-cell sums) ----

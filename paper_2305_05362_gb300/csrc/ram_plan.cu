@@ -295,6 +295,10 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
     p->n_cells = ro[nr];
     p->flags = desc->flags;
     p->limiter = (desc->flags & RAM_LIMITER_OFF) ? 0 : 1;
+    // FP32 warp-segment rows default to the shared-memory ring form, 3 warps per
+    // row CTA (the fastest measured on the disks; the autotuner may change it)
+    p->seg_variant = 2;
+    p->seg_warps = 3;
     p->row_offset.assign(ro, ro + nr + 1);
     const size_t n_nodes = shared ? (size_t)(ro[1] + 1) : (size_t)(ro[nr] + nr);
     p->nodes_h.assign(desc->nodes, desc->nodes + n_nodes);
