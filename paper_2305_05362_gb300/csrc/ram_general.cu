@@ -405,15 +405,28 @@ __global__ void __launch_bounds__(512)
     block_scan<T>(sQ, sDX, kHR, W - kHR, sS, wt);
 
     // ---- shifted edges: source cell, offset, in-cell cumulative (Eq. 16) ----
-    for (int j = tid; j <= nq; j += nth) {
+    // A thread takes a contiguous run of edges: the first is located by binary
+    // search over the window's nodes, the next ones by walking on from there
+    // (shifted edges and nodes both increase; a whole-row tile's edges drop back
+    // once, at the seam, and are searched again).
+    const int ne = nq + 1;
+    const int per = (ne + nth - 1) / nth;
+    const int j0 = min(ne, tid * per), j1 = min(ne, j0 + per);
+    int lo = kHR;
+    for (int j = j0; j < j1; ++j) {
         const uint64_t y = sXo[j] - S - xbase;
-        int lo = kHR, hi = W - kHR;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sY[mid] <= y)
-                lo = mid;
-            else
-                hi = mid;
+        if (j == j0 || y < sY[lo]) {
+            lo = kHR;
+            int hi = W - kHR;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sY[mid] <= y)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+        } else {
+            while (lo + 1 < W - kHR && sY[lo + 1] <= y) ++lo;
         }
         const uint64_t d = y - sY[lo];
         const uint64_t width = sY[lo + 1] - sY[lo];

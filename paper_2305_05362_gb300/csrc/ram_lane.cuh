@@ -9,15 +9,6 @@
 
 namespace ram {
 
-// 1/x from the hardware reciprocal approximation (rcp.approx: relative error
-// about 2^-23; subnormal results flush to zero)
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 // a / b for the slope ratios of the uniform-row kernels: FP32 multiplies by the
 // approximate reciprocal (one instruction more than the product; the ratios'
 // denominators are sums of cell differences, far inside the FP32 range)
