@@ -420,7 +420,7 @@ template <int V>
 struct RingLayout {
     static constexpr int WQ = 32 * V + 12;
     static constexpr int WV = 32 * V;
-    static constexpr int S = V == 8 ? 4 : 3;
+    static constexpr int S = 4;
     static constexpr int stage_floats = WQ + WV;
     static constexpr int warp_bytes = S * stage_floats * 4;
     static_assert((stage_floats * 4) % 16 == 0, "16-byte aligned stages");
@@ -435,7 +435,7 @@ struct RingLayout {
 // before it when every row of the step takes this kernel; the phase is then
 // advanced here too (a.row_phase).  FP32 rows of at least 32 V + 12 cells.
 template <int ORDER, int V, bool LIM, bool VL>
-__global__ void __launch_bounds__(256, V == 8 ? 3 : 2)
+__global__ void __launch_bounds__(256, 3)
     k_useg_ring(StepArgs a, const int32_t *row_ids)
 {
     using L = RingLayout<V>;
