@@ -27,8 +27,8 @@
 namespace ram {
 namespace {
 
-constexpr int kHalo = 2 * RAM_MAX_NSUB;  // residual halo, cells per side (max)
-constexpr int kHR = 2;                   // reconstruction halo, cells per side
+constexpr int kHalo = kGenHalo;  // residual halo, cells per side (max)
+constexpr int kHR = kGenHR;      // reconstruction halo, cells per side
 
 // ---------------- compensated accumulation ----------------
 struct DF {
@@ -266,14 +266,15 @@ __device__ __forceinline__ T vl_slope_nu(const T *c, const T *w, int u)
 }
 
 // Byte offsets of the general kernel's shared arrays (window of wcap cells,
-// wcap + 1 nodes; qcap output cells, qcap + 1 edges); one function serves the
-// kernel's carve-up and the launcher's size.
+// wcap + 1 nodes; qcap output cells, qcap + 1 edges; the residual's arrays only
+// when a residual step runs); one function serves the kernel's carve-up and the
+// launcher's size.
 struct GLayout {
-    size_t sY, sS, sXo, sEy, wt, sQ, sDX, sEG, sDXo, sP, sP2, sV, sF, sEp, total;
+    size_t sY, sS, sXo, wt, sQ, sDX, sEG, sDXo, sP, sP2, sV, sF, sEp, total;
 };
 
 template <typename T>
-__host__ __device__ inline GLayout general_layout(int wcap, int qcap)
+__host__ __device__ inline GLayout general_layout(int wcap, int qcap, bool resid)
 {
     using A = typename Acc<T>::A;
     GLayout L;
@@ -286,16 +287,15 @@ __host__ __device__ inline GLayout general_layout(int wcap, int qcap)
     L.sY = put(sizeof(uint64_t) * (wcap + 1));
     L.sS = put(sizeof(A) * (wcap + 1));
     L.sXo = put(sizeof(uint64_t) * (qcap + 1));
-    L.sEy = put(sizeof(uint64_t) * (qcap + 1));
     L.wt = put(sizeof(A) * 32);
     L.sQ = put(sizeof(T) * wcap);
     L.sDX = put(sizeof(T) * wcap);
     L.sEG = put(sizeof(T) * (qcap + 1));
     L.sDXo = put(sizeof(T) * qcap);
     L.sP = put(sizeof(T) * qcap);
-    L.sP2 = put(sizeof(T) * qcap);
-    L.sV = put(sizeof(T) * (qcap + 1));
-    L.sF = put(sizeof(T) * (qcap + 1));
+    L.sP2 = put(resid ? sizeof(T) * qcap : 0);
+    L.sV = put(resid ? sizeof(T) * (qcap + 1) : 0);
+    L.sF = put(resid ? sizeof(T) * (qcap + 1) : 0);
     L.sEp = put(sizeof(int) * (qcap + 1));
     L.total = o;
     return L;
@@ -303,16 +303,15 @@ __host__ __device__ inline GLayout general_layout(int wcap, int qcap)
 
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(512)
-    k_general(StepArgs a, int wcap, int qcap, const RowParams<T> *pars)
+    k_general(StepArgs a, int wcap, int qcap, int resid, const RowParams<T> *pars)
 {
     using AC = Acc<T>;
     using A = typename AC::A;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const GLayout L = general_layout<T>(wcap, qcap);
+    const GLayout L = general_layout<T>(wcap, qcap, resid != 0);
     uint64_t *sY = reinterpret_cast<uint64_t *>(smem_raw + L.sY);    // wcap + 1
     A *sS = reinterpret_cast<A *>(smem_raw + L.sS);                  // wcap + 1
     uint64_t *sXo = reinterpret_cast<uint64_t *>(smem_raw + L.sXo);  // qcap + 1
-    uint64_t *sEy = reinterpret_cast<uint64_t *>(smem_raw + L.sEy);  // qcap + 1
     A *wt = reinterpret_cast<A *>(smem_raw + L.wt);                  // 32
     T *sQ = reinterpret_cast<T *>(smem_raw + L.sQ);                  // wcap
     T *sDX = reinterpret_cast<T *>(smem_raw + L.sDX);                // wcap
@@ -432,7 +431,6 @@ __global__ void __launch_bounds__(512)
         const uint64_t width = sY[lo + 1] - sY[lo];
         const T xi = Num<T>::div(u64_to(d, T(0)), u64_to(width, T(0)));
         sEp[j] = lo;
-        sEy[j] = y;
         sEG[j] = (d == 0) ? T(0) : cell_G<T, ORDER>(sQ, sDX, lo, xi, lim);
     }
     __syncthreads();
@@ -440,7 +438,7 @@ __global__ void __launch_bounds__(512)
     // ---- output masses (Eq. 18) and cell averages (Eq. 26) ----
     for (int j = tid; j < nq; j += nth) {
         const int pL = sEp[j], pR = sEp[j + 1];
-        const uint64_t yL = sEy[j], yR = sEy[j + 1];
+        const uint64_t yL = sXo[j] - S - xbase, yR = sXo[j + 1] - S - xbase;
         const bool wrap = whole && (yR <= yL);
         const T GL = sEG[j], GR = sEG[j + 1];
         T val;
@@ -509,18 +507,12 @@ __global__ void __launch_bounds__(512)
 }
 
 template <typename T, int ORDER>
-cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s)
+cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t s, int first,
+                                 int count, int wcap, int qcap)
 {
-    const std::vector<Tile> &th = p.tiles_general_h[ORDER];
-    if (th.empty()) return cudaSuccess;
-    int wcap = 0, cnt = 0;
-    for (const Tile &t : th) {
-        const int w = t.window == 0 ? p.rows_h[t.row].n + 2 * kHR : t.window;
-        wcap = w > wcap ? w : wcap;
-        cnt = t.count > cnt ? t.count : cnt;
-    }
-    const int qcap = cnt + 2 * kHalo;
-    const size_t smem = general_layout<T>(wcap, qcap).total;
+    if (count == 0) return cudaSuccess;
+    const bool resid = a0.mode != MODE_SHIFT && a0.dv != nullptr;
+    const size_t smem = general_layout<T>(wcap, qcap, resid).total;
     if (smem > 227 * 1024) return cudaErrorNotSupported;
     static size_t configured[64] = {0};
     const int dev = p.device < 64 ? p.device : 63;
@@ -532,12 +524,27 @@ cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s)
         configured[dev] = smem;
     }
     StepArgs a = a0;
-    a.tiles = p.tiles_general[ORDER];
-    a.n_tiles = (int)th.size();
+    a.tiles = p.tiles_general[ORDER] + first;
+    a.n_tiles = count;
     // the plan's threads per CTA (every phase of a tile strides over its cells)
     const int threads = p.threads < 512 ? p.threads : 512;
-    return launch_pdl(k_general<T, ORDER>, (int)th.size(), threads, smem, s, a, wcap, qcap,
-                      static_cast<const RowParams<T> *>(p.row_par));
+    return launch_pdl(k_general<T, ORDER>, count, threads, smem, s, a, wcap, qcap,
+                      resid ? 1 : 0, static_cast<const RowParams<T> *>(p.row_par));
+}
+
+// Whole-row tiles (short rows) and windowed tiles run as two launches, each with
+// the shared memory of its own largest tile (plan-time sizes).
+template <typename T, int ORDER>
+cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s)
+{
+    const int n = (int)p.tiles_general_h[ORDER].size();
+    if (n == 0) return cudaSuccess;
+    const int nw = p.gen_whole[ORDER];
+    cudaError_t e = launch_general_class<T, ORDER>(p, a0, s, 0, nw, p.gen_wcap[0][ORDER],
+                                                   p.gen_qcap[0][ORDER]);
+    if (e != cudaSuccess) return e;
+    return launch_general_class<T, ORDER>(p, a0, s, nw, n - nw, p.gen_wcap[1][ORDER],
+                                          p.gen_qcap[1][ORDER]);
 }
 
 // ---------------- per-row mass (Eq. 10) ----------------

@@ -51,6 +51,11 @@ struct Tile {
     int32_t window;       // bound on the source-window cells (non-uniform tiles)
 };
 
+// Non-uniform tiles: residual halo (cells per side, the most sub-steps) and
+// reconstruction halo (cells per side) of the general kernel.
+constexpr int kGenHalo = 2 * RAM_MAX_NSUB;
+constexpr int kGenHR = 2;
+
 // Tries of a bounded device-side wait before it gives up and records a timeout.
 constexpr uint32_t kWaitLimit = 1u << 20;
 
@@ -110,7 +115,12 @@ struct Plan {
     std::vector<RowInfo> rows_h;
     std::vector<double> nodes_h;   // host copy of the FP64 nodes (per row or shared)
     std::vector<Tile> tiles_uniform_h[5];  // by order (index 2..4): every uniform row
-    std::vector<Tile> tiles_general_h[5];
+    std::vector<Tile> tiles_general_h[5];  // whole-row tiles first, then windowed ones
+    // per order: whole-row tiles, and for (whole-row, windowed) tiles the largest
+    // source window and output extent (cells) the general kernel stages
+    int32_t gen_whole[5] = {0};
+    int32_t gen_wcap[2][5] = {{0}};
+    int32_t gen_qcap[2][5] = {{0}};
     // uniform rows taken by the persistent whole-row kernel, per dtype and order, and
     // the tiles of the remaining uniform rows
     std::vector<int32_t> rows_fit_h[2][5];

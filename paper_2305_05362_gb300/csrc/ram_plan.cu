@@ -134,7 +134,7 @@ ram_status build_tiles(Plan &p)
         }
     }
     p.window_max = 0;
-    const int halo_res = 2 * RAM_MAX_NSUB;  // residual halo, cells per side
+    const int halo_res = kGenHalo;  // residual halo, cells per side
     const int tg = std::max(64, p.tile_cells / 2);  // output cells per non-uniform tile
     for (int r = 0; r < p.n_rows; ++r) {
         const RowInfo &ri = p.rows_h[r];
@@ -229,6 +229,19 @@ ram_status build_tiles(Plan &p)
         }
     }
     for (int o = 2; o <= 4; ++o) {
+        // the general kernel runs whole-row tiles (window 0) and windowed tiles as
+        // two launches, each with the shared memory its own largest tile needs
+        std::vector<Tile> &tg_o = p.tiles_general_h[o];
+        std::stable_partition(tg_o.begin(), tg_o.end(), [](const Tile &t) { return t.window == 0; });
+        p.gen_whole[o] = 0;
+        for (int c = 0; c < 2; ++c) p.gen_wcap[c][o] = p.gen_qcap[c][o] = 0;
+        for (const Tile &t : tg_o) {
+            const int c = t.window == 0 ? 0 : 1;
+            if (c == 0) ++p.gen_whole[o];
+            const int w = c == 0 ? p.rows_h[t.row].n + 2 * kGenHR : t.window;
+            p.gen_wcap[c][o] = std::max(p.gen_wcap[c][o], w);
+            p.gen_qcap[c][o] = std::max(p.gen_qcap[c][o], t.count + 2 * kGenHalo);
+        }
         if (upload(&p.tiles_uniform[o], p.tiles_uniform_h[o].data(),
                    p.tiles_uniform_h[o].size()) != cudaSuccess)
             return RAM_ERR_NOMEM;
