@@ -303,7 +303,7 @@ __host__ __device__ inline GLayout general_layout(int wcap, int qcap, bool resid
 
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(512)
-    k_general(StepArgs a, int wcap, int qcap, int resid, const RowParams<T> *pars)
+    k_general(StepArgs a, int wcap, int qcap, int resid, int wait, const RowParams<T> *pars)
 {
     using AC = Acc<T>;
     using A = typename AC::A;
@@ -338,7 +338,11 @@ __global__ void __launch_bounds__(512)
     T *qout = static_cast<T *>(a.q_out) + row.cell_off;
     const bool lim = a.limiter != 0;
 
-    pdl_wait();
+    // The first general launch of a step waits for the parameter kernel; the
+    // later ones are launched once it has (each launch lets the next start as
+    // soon as its own wait is over) and touch other rows, so they run alongside.
+    if (wait) pdl_wait();
+    pdl_trigger();
     const RowParams<T> P = pars[tile.row];
     const uint64_t S = P.sfix;
     const int nsub = P.nsub;
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(512)
 
 template <typename T, int ORDER>
 cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t s, int first,
-                                 int count, int wcap, int qcap)
+                                 int count, int wcap, int qcap, int &launched)
 {
     if (count == 0) return cudaSuccess;
     const bool resid = a0.mode != MODE_SHIFT && a0.dv != nullptr;
@@ -528,23 +532,26 @@ cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t
     a.n_tiles = count;
     // the plan's threads per CTA (every phase of a tile strides over its cells)
     const int threads = p.threads < 512 ? p.threads : 512;
-    return launch_pdl(k_general<T, ORDER>, count, threads, smem, s, a, wcap, qcap,
-                      resid ? 1 : 0, static_cast<const RowParams<T> *>(p.row_par));
+    cudaError_t e = launch_pdl(k_general<T, ORDER>, count, threads, smem, s, a, wcap, qcap,
+                               resid ? 1 : 0, launched == 0 ? 1 : 0,
+                               static_cast<const RowParams<T> *>(p.row_par));
+    if (e == cudaSuccess) ++launched;
+    return e;
 }
 
 // Whole-row tiles (short rows) and windowed tiles run as two launches, each with
 // the shared memory of its own largest tile (plan-time sizes).
 template <typename T, int ORDER>
-cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s)
+cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, int &launched)
 {
     const int n = (int)p.tiles_general_h[ORDER].size();
     if (n == 0) return cudaSuccess;
     const int nw = p.gen_whole[ORDER];
     cudaError_t e = launch_general_class<T, ORDER>(p, a0, s, 0, nw, p.gen_wcap[0][ORDER],
-                                                   p.gen_qcap[0][ORDER]);
+                                                   p.gen_qcap[0][ORDER], launched);
     if (e != cudaSuccess) return e;
     return launch_general_class<T, ORDER>(p, a0, s, nw, n - nw, p.gen_wcap[1][ORDER],
-                                          p.gen_qcap[1][ORDER]);
+                                          p.gen_qcap[1][ORDER], launched);
 }
 
 // ---------------- per-row mass (Eq. 10) ----------------
@@ -579,14 +586,15 @@ __global__ void __launch_bounds__(256) k_mass(const RowInfo *rows, const float *
 cudaError_t launch_general(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
+    int launched = 0;  // general launches so far in this step
     if (dt == RAM_F32) {
-        if ((e = launch_general_t<float, 2>(p, a, s)) != cudaSuccess) return e;
-        if ((e = launch_general_t<float, 3>(p, a, s)) != cudaSuccess) return e;
-        return launch_general_t<float, 4>(p, a, s);
+        if ((e = launch_general_t<float, 2>(p, a, s, launched)) != cudaSuccess) return e;
+        if ((e = launch_general_t<float, 3>(p, a, s, launched)) != cudaSuccess) return e;
+        return launch_general_t<float, 4>(p, a, s, launched);
     }
-    if ((e = launch_general_t<double, 2>(p, a, s)) != cudaSuccess) return e;
-    if ((e = launch_general_t<double, 3>(p, a, s)) != cudaSuccess) return e;
-    return launch_general_t<double, 4>(p, a, s);
+    if ((e = launch_general_t<double, 2>(p, a, s, launched)) != cudaSuccess) return e;
+    if ((e = launch_general_t<double, 3>(p, a, s, launched)) != cudaSuccess) return e;
+    return launch_general_t<double, 4>(p, a, s, launched);
 }
 
 cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *out,
