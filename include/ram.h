@@ -111,7 +111,10 @@ ram_status ram_residual_upwind(ram_plan plan, ram_dtype dtype, const void *q_in,
  * residual step with dv_iface (NULL -> dv = 0, no residual).  v0: device FP64
  * per row.  phase: device FP64 per row, or NULL; when given, phase[r] is
  * replaced by (phase[r] + s_r) reduced to [0, L_r), the accumulated offset
- * v0 t mod L of the row. */
+ * v0 t mod L of the row (always in FP64).  The cell shift s_r N_r / L_r is
+ * formed in FP64, except on FP32 rows of the shared-memory ring form of the
+ * warp-segment kernel, which form it in two-float arithmetic (about 2^-46
+ * relative) and treat a shift of 2^40 cells or more as non-finite. */
 ram_status ram_step(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
                     double *phase, const double *v0, double dt, const void *dv_iface,
                     ram_scheme scheme, const int32_t *nsub, void *stream);
