@@ -510,6 +510,110 @@ __global__ void __launch_bounds__(512)
     for (int i = tid; i < T_out; i += nth) qout[tile.start + i] = cur[H + i];
 }
 
+// The shift step alone (no residual) on non-uniform rows, without shared
+// memory: the warps of a CTA split a tile's output cells into chunks of 32 V,
+// lane l taking V consecutive cells.  Per output edge a lane locates the source
+// cell of the shifted node (the bucket table for its first edge, then a walk
+// along the row's nodes; Eq. 16), gathers the cell's stencil from global memory
+// (cached) and evaluates the in-cell cumulative (cell_G); per output cell it
+// sums the whole source cells between its two edges directly (Eq. 18, in the
+// order of the cells) and divides by the cell's width (Eq. 26).  No barriers:
+// the warps and CTAs interleave their loads and arithmetic freely.
+template <typename T, int ORDER, int V>
+__global__ void __launch_bounds__(512)
+    k_gwarp(StepArgs a, int wait, const RowParams<T> *pars)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const Tile tile = a.tiles[blockIdx.x];
+    const RowInfo row = a.rows[tile.row];
+    const int N = row.n;
+    const uint64_t *X = a.xfix + row.mesh_off;
+    const T *DX = (sizeof(T) == 4) ? reinterpret_cast<const T *>(a.dx32 + row.mesh_off)
+                                   : reinterpret_cast<const T *>(a.dx64 + row.mesh_off);
+    const int32_t *bt = a.buckets + row.bucket_off;
+    const T *qin = static_cast<const T *>(a.q_in) + row.cell_off;
+    T *qout = static_cast<T *>(a.q_out) + row.cell_off;
+    const bool lim = a.limiter != 0;
+
+    if (wait) pdl_wait();
+    pdl_trigger();
+    const uint64_t S = pars[tile.row].sfix;
+    constexpr int HS = ORDER == 2 ? 1 : 2;  // stencil half-width of cell_G
+
+    for (int c0 = warp * 32 * V; c0 < tile.count; c0 += nwarps * 32 * V) {
+        const int i0 = c0 + lane * V;  // this lane's first output cell in the tile
+        const int nc = min(V, tile.count - i0);
+        if (nc <= 0) continue;
+        // the lane's nc + 1 edges: source cell, shifted position, in-cell cumulative
+        int pe[V + 1];
+        uint64_t ye[V + 1];
+        T G[V + 1];
+        int p = 0;
+        uint64_t yprev = 0;
+#pragma unroll
+        for (int k = 0; k <= V; ++k) {
+            if (k > nc) break;
+            const int e = wrap_index((int64_t)tile.start + i0 + k, N);
+            const uint64_t y = X[e] - S;
+            if (k == 0 || y < yprev) {
+                p = locate_row(X, N, bt, row.bucket_bits, y);
+            } else {
+                while (p + 1 < N && X[p + 1] <= y) ++p;
+            }
+            yprev = y;
+            const uint64_t xp = X[p];
+            const uint64_t xn = p + 1 < N ? X[p + 1] : 0ull;  // the period's end is 2^64 = 0
+            const uint64_t d = y - xp;
+            pe[k] = p;
+            ye[k] = y;
+            if (d == 0) {
+                G[k] = T(0);
+            } else {
+                T qs[2 * HS + 1], ds[2 * HS + 1];
+#pragma unroll
+                for (int u = 0; u <= 2 * HS; ++u) {
+                    const int c = wrap_index((int64_t)p - HS + u, N);
+                    qs[u] = qin[c];
+                    ds[u] = DX[c];
+                }
+                const T xi = Num<T>::div(u64_to(d, T(0)), u64_to(xn - xp, T(0)));
+                G[k] = cell_G<T, ORDER>(qs, ds, HS, xi, lim);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            if (k >= nc) break;
+            const int g = wrap_index((int64_t)tile.start + i0 + k, N);  // output cell
+            const int pL = pe[k], pR = pe[k + 1];
+            const uint64_t dL = ye[k] - X[pL], dR = ye[k + 1] - X[pR];
+            const uint64_t wsrc = (pL + 1 < N ? X[pL + 1] : 0ull) - X[pL];
+            const uint64_t wout = (g + 1 < N ? X[g + 1] : 0ull) - X[g];
+            const int pnext = pL + 1 < N ? pL + 1 : 0;
+            T val;
+            if (dL == 0 && dR == 0 && pR == pnext && pL != pR && wsrc == wout) {
+                val = qin[pL];  // the output cell is exactly one source cell: copy it
+            } else {
+                T mass;
+                if (pL == pR && dR > dL) {
+                    mass = G[k + 1] - G[k];  // inside one source cell
+                } else {
+                    // the rest of cell pL, the whole cells up to pR (cyclic), the start of pR
+                    mass = qin[pL] * DX[pL] - G[k];
+                    int m = pnext;
+                    while (m != pR) {
+                        mass += qin[m] * DX[m];
+                        m = m + 1 < N ? m + 1 : 0;
+                    }
+                    mass += G[k + 1];
+                }
+                val = Num<T>::div(mass, DX[g]);
+            }
+            qout[g] = val;
+        }
+    }
+}
+
 template <typename T, int ORDER>
 cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t s, int first,
                                  int count, int wcap, int qcap, int &launched)
@@ -546,6 +650,18 @@ cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, 
 {
     const int n = (int)p.tiles_general_h[ORDER].size();
     if (n == 0) return cudaSuccess;
+    if (a0.mode == MODE_SHIFT || a0.dv == nullptr) {
+        // no residual: the shared-memory-free kernel takes every tile in one launch
+        StepArgs a = a0;
+        a.tiles = p.tiles_general[ORDER];
+        a.n_tiles = n;
+        const int threads = p.threads < 512 ? p.threads : 512;
+        cudaError_t e = launch_pdl(k_gwarp<T, ORDER, 4>, n, threads, 0, s, a,
+                                   launched == 0 ? 1 : 0,
+                                   static_cast<const RowParams<T> *>(p.row_par));
+        if (e == cudaSuccess) ++launched;
+        return e;
+    }
     const int nw = p.gen_whole[ORDER];
     cudaError_t e = launch_general_class<T, ORDER>(p, a0, s, 0, nw, p.gen_wcap[0][ORDER],
                                                    p.gen_qcap[0][ORDER], launched);
