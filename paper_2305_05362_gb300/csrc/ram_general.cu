@@ -554,7 +554,9 @@ __global__ void __launch_bounds__(512)
 #pragma unroll
         for (int k = 0; k <= V; ++k) {
             if (k > nc) break;
-            const int e = wrap_index((int64_t)tile.start + i0 + k, N);
+            // edge nodes run from tile.start to at most N (node N is node 0)
+            const int en = tile.start + i0 + k;
+            const int e = en < N ? en : en - N;
             const uint64_t y = X[e] - S;
             if (k == 0 || y < yprev) {
                 p = locate_row(X, N, bt, row.bucket_bits, y);
@@ -571,11 +573,19 @@ __global__ void __launch_bounds__(512)
                 G[k] = T(0);
             } else {
                 T qs[2 * HS + 1], ds[2 * HS + 1];
+                if (p >= HS && p + HS < N) {
 #pragma unroll
-                for (int u = 0; u <= 2 * HS; ++u) {
-                    const int c = wrap_index((int64_t)p - HS + u, N);
-                    qs[u] = qin[c];
-                    ds[u] = DX[c];
+                    for (int u = 0; u <= 2 * HS; ++u) {
+                        qs[u] = qin[p - HS + u];
+                        ds[u] = DX[p - HS + u];
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u <= 2 * HS; ++u) {
+                        const int c = wrap_index((int64_t)p - HS + u, N);
+                        qs[u] = qin[c];
+                        ds[u] = DX[c];
+                    }
                 }
                 const T xi = Num<T>::div(u64_to(d, T(0)), u64_to(xn - xp, T(0)));
                 G[k] = cell_G<T, ORDER>(qs, ds, HS, xi, lim);
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(512)
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             if (k >= nc) break;
-            const int g = wrap_index((int64_t)tile.start + i0 + k, N);  // output cell
+            const int g = tile.start + i0 + k;  // output cell (< N)
             const int pL = pe[k], pR = pe[k + 1];
             const uint64_t dL = ye[k] - X[pL], dR = ye[k + 1] - X[pR];
             const uint64_t wsrc = (pL + 1 < N ? X[pL + 1] : 0ull) - X[pL];
