@@ -1,6 +1,10 @@
 // RAM step on rows with their own non-uniform mesh (Sec. 3 on an arbitrary
 // periodic mesh), and the per-row mass diagnostic.
 //
+// Steps without a residual run k_gwarp (below): warps split each tile, each lane
+// locates its own edges and gathers the source stencils from the cache, with no
+// shared memory or barriers.  Steps with a residual run k_general:
+//
 // One CTA per tile of output cells.  The tile's source window -- the source
 // cells its shifted edges land in, plus the reconstruction halo -- is found
 // from the plan's bucket table (the index function of Sec. 3.2.1 tabulated on
@@ -10,14 +14,16 @@
 //   - the prefix sum of the window's cell masses M = Q dx (Eq. 3): a block scan,
 //     two-float compensated for FP32 cells (exact products, ~48-bit sums), FP64
 //     for FP64 cells;
-//   - every shifted edge is located by binary search in the window (Eq. 16) and
-//     the in-cell cumulative G_p(d) of its source cell's reconstruction is
+//   - every shifted edge is located in the window (Eq. 16; a binary search for
+//     the first of a thread's run of edges, a walk for the others) and the
+//     in-cell cumulative G_p(d) of its source cell's reconstruction is
 //     evaluated (PLM / PPM of App. A / order 4);
 //   - each output cell's mass is Eq. 18: right part of p(i), the whole cells in
 //     between as a difference of the scan, left part of p(i+1); Q = M / dx
 //     (Eq. 26);
 //   - the residual sub-steps (Eq. 6) with per-cell widths.
-// Short rows are one tile covering the whole row cyclically.
+// Short rows are one tile covering the whole row cyclically (a launch of their
+// own, sized for the largest of them).
 #include <cuda_runtime.h>
 
 #include <cstdint>
