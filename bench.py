@@ -386,7 +386,12 @@ def main():
     step_s = total_s / args.steps
     achieved = w.n_cells * bpc / step_s / 1e9
     peak, peak_kind = _peaks()
-    kernel_key = _kernel_name(tuning) if info.n_tiles_general == 0 else "k_general<float>"
+    # the dominant kernel: the uniform-row kernel the tuning selects, else the
+    # non-uniform rows' kernel (shared-memory-free without a residual, tiled with one)
+    if info.n_tiles_general == 0:
+        kernel_key = _kernel_name(tuning)
+    else:
+        kernel_key = "k_gwarp<float>" if w.dv is None else "k_general<float>"
     tr = _traffic(kernel_key + ":" + w.name)
 
     # FP64 form of the same step, and the FP32-vs-FP64 error after the same steps
