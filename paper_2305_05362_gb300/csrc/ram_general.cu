@@ -672,7 +672,7 @@ cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, 
         a.tiles = p.tiles_general[ORDER];
         a.n_tiles = n;
         const int threads = p.threads < 512 ? p.threads : 512;
-        cudaError_t e = launch_pdl(k_gwarp<T, ORDER, 4>, n, threads, 0, s, a,
+        cudaError_t e = launch_pdl(k_gwarp<T, ORDER, 2>, n, threads, 0, s, a,
                                    launched == 0 ? 1 : 0,
                                    static_cast<const RowParams<T> *>(p.row_par));
         if (e == cudaSuccess) ++launched;
