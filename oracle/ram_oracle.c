@@ -16,7 +16,7 @@
  *   Eqs. 5-6        operator splitting: shift first, then the residual dv step
  * plus a hand-derived transpose of the linear (limiter-off, donor) step.
  *
- * Readings of points where the paper is silent or garbled (listed in the design doc):
+ * Readings of points where the paper is silent or garbled:
  *   - content moves by +s (x~ = x - s, Sec. 3.2); s is reduced with a floor-mod.
  *   - an edge exactly on a node belongs to the cell on its right (the <= of Eq. 16).
  *   - App. A weights omega~_1..3 are read with SUMS of widths where the text prints
