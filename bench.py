@@ -228,6 +228,232 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _dominant_kernel(info, w, tuning):
+    """The kernel that takes the step's time, as ncu names it: the uniform-row
+    kernel the tuning selects, else the non-uniform rows' kernel."""
+    if info.n_tiles_general == 0:
+        return _kernel_name(tuning)
+    return "k_gwarp<float>" if w.dv is None else "k_general<float>"
+
+
+class Runner:
+    """One workload on this rank's GPU: its plan, device tensors and the timed
+    loop (CUDA events on the launching stream, L2 flushed before every step)."""
+
+    def __init__(self, w, dev, world, args, tuning=None, autotune=True):
+        import torch
+        from paper_2305_05362_gb300 import ram
+        self.torch, self.ram = torch, ram
+        self.w, self.dev, self.world, self.args = w, dev, world, args
+        self.plan = ram.Plan.from_workload(w, device=dev.index)
+        self.info = self.plan.info()
+        self.v0 = torch.tensor(w.v0, dtype=torch.float64, device=dev)
+        self.nsub = torch.tensor(w.nsub, dtype=torch.int32, device=dev)
+        if tuning:
+            t = self.plan.tuning()
+            for k, v in tuning.items():
+                setattr(t, k, int(v))
+            self.plan.set_tuning(t)
+        elif autotune:
+            for dt_ in (torch.float64, torch.float32):
+                q_, _, dv_ = self.tensors(dt_)
+                ram.autotune(self.plan, q_, torch.empty_like(q_), self.v0, w.dt, dv=dv_,
+                             scheme=w.scheme, nsub=self.nsub, reps=10)
+                del q_, dv_
+        props = torch.cuda.get_device_properties(dev)
+        l2 = int(getattr(props, "L2_cache_size", 0) or 0)
+        self.flush_buf = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+        self.flush_buf.fill_(1.0)
+
+    def tensors(self, dtype):
+        torch, w = self.torch, self.w
+        q = torch.tensor(np.asarray(w.q0), dtype=dtype, device=self.dev)
+        dv = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dtype, device=self.dev)
+        return q, torch.empty_like(q), dv
+
+    def step(self, q, out, dv):
+        w = self.w
+        self.ram.step(self.plan, q, out, self.v0, w.dt, dv=dv, scheme=w.scheme, nsub=self.nsub)
+
+    def timed(self, dtype, steps, warm):
+        torch, w = self.torch, self.w
+        import torch.distributed as dist
+        q, out, dv = self.tensors(dtype)
+        for _ in range(warm):
+            self.step(q, out, dv)
+            q, out = out, q
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        # host cost of enqueueing one timed step, so that a sleep kernel can hold
+        # the GPU until the whole timed loop is queued (the events then time the
+        # kernels, not the Python launch path)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            self.flush_buf.sum()
+            self.step(q, out, dv)
+            q, out = out, q
+        host_per_step = (time.perf_counter() - t0) / 5
+        torch.cuda.synchronize()
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        hold_s = min(20.0, 2.0 * host_per_step * steps + 0.05)
+        if not self.args.no_hold:
+            torch.cuda._sleep(int(hold_s * 2.1e9))
+        for k in range(steps):
+            self.flush_buf.sum()  # a read of 2 x L2 bytes evicts the step's data
+            ev[k][0].record()
+            self.step(q, out, dv)
+            ev[k][1].record()
+            q, out = out, q
+        torch.cuda.synchronize()
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        return q, [a.elapsed_time(b) for a, b in ev]
+
+    def refine_uniform(self):
+        """The autotuner times warm-cache repeats; the timed steps run on a cold L2,
+        which can rank the warp-segment launch shapes differently.  Refine them
+        under this loop's own protocol (median of 30 flushed steps each)."""
+        if self.info.n_uniform_rows != self.w.n_rows:
+            return
+        torch = self.torch
+        base = self.plan.tuning()
+        cands = [None] + [(v, g) for v in (0, 1, 2) for g in (3, 4, 6, 8)]
+        best, best_ms = None, float("inf")
+        for c in cands:
+            t = self.plan.tuning()
+            for f, _ in t._fields_:
+                setattr(t, f, getattr(base, f))
+            if c is not None:
+                t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, c[0], c[1]
+            self.plan.set_tuning(t)
+            _, ms_c = self.timed(torch.float32, 30, 3)
+            med = statistics.median(ms_c)
+            if med < best_ms:
+                best, best_ms = c, med
+        t = self.plan.tuning()
+        for f, _ in t._fields_:
+            setattr(t, f, getattr(base, f))
+        if best is not None:
+            t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, best[0], best[1]
+        self.plan.set_tuning(t)
+
+    def launches_per_step(self):
+        """Kernels of this library per step: the parameter kernel (none when every
+        row is a warp-segment row of the shared-memory ring kernel, which forms its
+        own), one launch per order present among the uniform rows, and the
+        non-uniform rows' launch."""
+        w, info, t = self.w, self.info, self.plan.tuning().as_dict()
+        uniform_orders = {int(o) for o in w.order} if info.n_uniform_rows else set()
+        lens = np.diff(np.asarray(w.row_offset))
+        all_seg = (info.n_uniform_rows == w.n_rows and bool(np.all(lens >= 512))
+                   and bool(np.all(lens % 4 == 0))
+                   and bool(np.all(np.asarray(w.row_offset) % 4 == 0)))
+        own = all_seg and t["uniform_kernel_f32"] == 1 and t["seg_variant_f32"] == 2
+        general = {int(o) for o, n in zip(w.order, lens)} if info.n_tiles_general else set()
+        return (0 if own else 1) + len(uniform_orders) + len(general)
+
+    def record(self, steps, warmup, rank, with_fp64=True, fp64_steps=50):
+        """Timed FP32 run with its clock sample and roofline; the FP64 form of the
+        same step and the FP32-vs-FP64 relative L1 after the same steps."""
+        torch, w, world = self.torch, self.w, self.world
+        sampler = ClockSampler(_uuid(self.dev) if rank == 0 else None)
+        if rank == 0:
+            sampler.start()
+        q32, ms32 = self.timed(torch.float32, steps, warmup)
+        clocks = sampler.stop() if rank == 0 else None
+        st = self.plan.check_errors()
+        from paper_2305_05362_gb300 import shard
+        total_s = sum(ms32) / 1e3
+        total_max = shard.global_max(total_s)
+        value = w.n_cells * world * steps / total_max / 1e9
+        bpc = _bytes_per_cell(w, 4)
+        step_s = total_s / steps
+        achieved = w.n_cells * bpc / step_s / 1e9
+        peak, peak_kind = _peaks()
+        tuning = self.plan.tuning().as_dict()
+        kernel_key = _dominant_kernel(self.info, w, tuning)
+        tr = _traffic(kernel_key + ":" + w.name)
+        rec = {"workload": w.name, "rows": w.n_rows, "cells": w.n_cells, "value": value,
+               "unit": UNIT, "steps": steps, "ms_per_step": 1e3 * total_max / steps,
+               "gpu_launches": int(steps * self.launches_per_step()),
+               "roofline": {"bound": "hbm", "kernel": kernel_key, "achieved": achieved,
+                            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                            "peak_kind": peak_kind, "bytes_per_cell": bpc,
+                            "traffic": None if tr is None else tr["dram_bytes_per_launch"]},
+               "clocks": clocks, "device_status": st, "tuning": tuning,
+               "l2": "read of 2x L2 before every timed step; step time = sum of per-step "
+                     "CUDA-event intervals"}
+        if with_fp64:
+            n64 = min(fp64_steps, steps)
+            q64, ms64 = self.timed(torch.float64, n64, 3)
+            q32b, _ = self.timed(torch.float32, n64, 3)
+            a, b = q32b.double(), q64
+            rec["fp64_same_launch"] = {
+                "value": w.n_cells * n64 / (sum(ms64) / 1e3) / 1e9, "unit": UNIT, "steps": n64,
+                "form": "the same step in FP64 (cells and arithmetic), autotuned",
+                "rel_l1_fp32_vs_fp64": float((a - b).abs().sum() / b.abs().sum())}
+            del q64, q32b
+        return rec, q32
+
+    def close(self):
+        self.plan.destroy()
+        del self.flush_buf
+
+
+def _uuid(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def fp64_single_problem(w, dev, steps=10):
+    """The plain FP64 single-problem form: every row is its own problem with its
+    own plan, and every problem is its own launch, one after another, FP64
+    cells and arithmetic (no batching).  Returns Gcell-updates/s."""
+    import torch
+    from paper_2305_05362_gb300 import ram
+    plans, bufs = [], []
+    for r in range(w.n_rows):
+        x = w.row_nodes(r)
+        n = x.size - 1
+        p = ram.Plan([0, n], x, order=int(w.order[r]), limiter=w.limiter, device=dev.index)
+        q = torch.tensor(np.asarray(w.q0[w.row_slice(r)]), dtype=torch.float64, device=dev)
+        dv = (None if w.dv is None else
+              torch.tensor(np.asarray(w.dv[w.row_slice(r)]), dtype=torch.float64, device=dev))
+        v0 = torch.tensor([w.v0[r]], dtype=torch.float64, device=dev)
+        ns = torch.tensor([w.nsub[r]], dtype=torch.int32, device=dev)
+        plans.append(p)
+        bufs.append((q, torch.empty_like(q), dv, v0, ns))
+
+    def one_step():
+        for p, (q, out, dv, v0, ns) in zip(plans, bufs):
+            ram.step(p, q, out, v0, w.dt, dv=dv, scheme=w.scheme, nsub=ns)
+
+    for _ in range(3):
+        one_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one_step()
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    for p in plans:
+        p.destroy()
+    return {"value": w.n_cells * steps / s / 1e9, "unit": UNIT, "steps": steps,
+            "launches_per_step": int(w.n_rows),
+            "form": "one FP64 plan and one launch per problem (row), problems one after "
+                    "another on one stream"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,6 +463,8 @@ def main():
     ap.add_argument("--workload", default="disk", choices=["disk", "disk_large", "batched", "batched_large"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra records (batched rows, the large disk)")
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--tuning", default=None,
                     help="launch shapes as JSON (the tuning dict of an earlier line) instead of "
@@ -253,7 +481,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2305_05362_gb300 import ram, shard
+    from paper_2305_05362_gb300 import ram
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -265,169 +493,28 @@ def main():
 
     disk = tuple(int(x) for x in args.disk.split(",")) if args.disk else None
     w = _workload(args.workload, rank, disk)
-    plan = ram.Plan.from_workload(w, device=local)
-    info = plan.info()
-    # kernels of this library per step: the parameter kernel (none when every row
-    # is a warp-segment row of the shared-memory ring kernel, which forms its
-    # own), then one launch per order present among the uniform rows, plus the
-    # non-uniform tiles' kernel
-    uniform_orders = {int(o) for r, o in enumerate(w.order)} if info.n_uniform_rows else set()
-    lens = np.diff(np.asarray(w.row_offset))
-    all_seg = (info.n_uniform_rows == w.n_rows and bool(np.all(lens >= 512))
-               and bool(np.all(lens % 4 == 0)) and bool(np.all(np.asarray(w.row_offset) % 4 == 0)))
-
-    def launches_per_step(t):
-        own = all_seg and t["uniform_kernel_f32"] == 1 and t["seg_variant_f32"] == 2
-        return (0 if own else 1) + len(uniform_orders) + (1 if info.n_tiles_general else 0)
-
-    def tensors(dtype):
-        q = torch.tensor(np.asarray(w.q0), dtype=dtype, device=dev)
-        dv = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dtype, device=dev)
-        return q, torch.empty_like(q), dv
-
-    v0 = torch.tensor(w.v0, dtype=torch.float64, device=dev)
-    nsub = torch.tensor(w.nsub, dtype=torch.int32, device=dev)
-    # autotune the launch shapes once for each dtype (outside the timed region)
-    if args.tuning:
-        t = plan.tuning()
-        for k, v in json.loads(args.tuning).items():
-            setattr(t, k, int(v))
-        plan.set_tuning(t)
-    else:
-        for dt_ in (torch.float64, torch.float32):
-            q_ = torch.tensor(np.asarray(w.q0), dtype=dt_, device=dev)
-            dv_ = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dt_, device=dev)
-            ram.autotune(plan, q_, torch.empty_like(q_), v0, w.dt, dv=dv_, scheme=w.scheme,
-                         nsub=nsub, reps=10)
-            del q_, dv_
-    tuning = plan.tuning().as_dict()
-    props = torch.cuda.get_device_properties(dev)
-    l2 = int(getattr(props, "L2_cache_size", 0) or 0)
-    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
-    flush.fill_(1.0)
-
-    def do_flush():
-        flush.sum()  # a read of 2 x L2 bytes evicts the step's data without dirty lines
-
-    def timed(dtype, steps, warm):
-        q, out, dv = tensors(dtype)
-        for _ in range(warm):
-            ram.step(plan, q, out, v0, w.dt, dv=dv, scheme=w.scheme, nsub=nsub)
-            q, out = out, q
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        # host cost of enqueueing one timed step, so that a sleep kernel can hold
-        # the GPU until the whole timed loop is queued (the events then time the
-        # kernels, not the Python launch path)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(5):
-            do_flush()
-            ram.step(plan, q, out, v0, w.dt, dv=dv, scheme=w.scheme, nsub=nsub)
-            q, out = out, q
-        host_per_step = (time.perf_counter() - t0) / 5
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        hold_s = min(20.0, 2.0 * host_per_step * steps + 0.05)
-        if not args.no_hold:
-            torch.cuda._sleep(int(hold_s * 2.1e9))
-        for k in range(steps):
-            do_flush()
-            ev[k][0].record()
-            ram.step(plan, q, out, v0, w.dt, dv=dv, scheme=w.scheme, nsub=nsub)
-            ev[k][1].record()
-            q, out = out, q
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return q, ms
-
-    # The autotuner times warm-cache repeats; the timed steps run on a cold L2
-    # (flushed before each step), which can rank the warp-segment launch shapes
-    # differently.  Refine them under the bench's own protocol (median of 30
-    # flushed steps each) before the timed run.
-    if not args.tuning and info.n_uniform_rows == w.n_rows:
-        base = plan.tuning()
-        cands = [None] + [(v, g) for v in (0, 1, 2) for g in (3, 4, 6, 8)]
-        best, best_ms = None, float("inf")
-        for c in cands:
-            t = plan.tuning()
-            for f, _ in t._fields_:
-                setattr(t, f, getattr(base, f))
-            if c is not None:
-                t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, c[0], c[1]
-            plan.set_tuning(t)
-            _, ms_c = timed(torch.float32, 30, 3)
-            med = statistics.median(ms_c)
-            if med < best_ms:
-                best, best_ms = c, med
-        t = plan.tuning()
-        for f, _ in t._fields_:
-            setattr(t, f, getattr(base, f))
-        if best is not None:
-            t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, best[0], best[1]
-        plan.set_tuning(t)
-        tuning = plan.tuning().as_dict()
-
-    # FP32 timed run
-    uuid = None
-    try:
-        uuid = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU-") else str(props.uuid)
-    except Exception:
-        uuid = None
-    sampler = ClockSampler(uuid if rank == 0 else None)
-    if rank == 0:
-        sampler.start()
-    q32, ms32 = timed(torch.float32, args.steps, args.warmup)
-    clocks = sampler.stop() if rank == 0 else None
-    st = plan.check_errors()
-    total_s = sum(ms32) / 1e3
-    total_max = shard.global_max(total_s)  # max over ranks (NCCL, host scalar)
-    cells_all = w.n_cells * world
-    value = cells_all * args.steps / total_max / 1e9
-    ms_per_step = 1e3 * total_max / args.steps
-
-    # roofline of the step kernel
-    es = 4
-    bpc = _bytes_per_cell(w, es)
-    step_s = total_s / args.steps
-    achieved = w.n_cells * bpc / step_s / 1e9
-    peak, peak_kind = _peaks()
-    # the dominant kernel: the uniform-row kernel the tuning selects, else the
-    # non-uniform rows' kernel (shared-memory-free without a residual, tiled with one)
-    if info.n_tiles_general == 0:
-        kernel_key = _kernel_name(tuning)
-    else:
-        kernel_key = "k_gwarp<float>" if w.dv is None else "k_general<float>"
-    tr = _traffic(kernel_key + ":" + w.name)
-
-    # FP64 form of the same step, and the FP32-vs-FP64 error after the same steps
-    n64 = min(args.fp64_steps, args.steps)
-    q64, ms64 = timed(torch.float64, n64, 3)
-    q32b, _ = timed(torch.float32, n64, 3)
-    a, b = q32b.double(), q64
-    rel = float((a - b).abs().sum() / b.abs().sum())
-    fp64_value = w.n_cells * n64 / (sum(ms64) / 1e3) / 1e9
+    tuning_arg = json.loads(args.tuning) if args.tuning else None
+    run = Runner(w, dev, world, args, tuning=tuning_arg)
+    if not tuning_arg:
+        run.refine_uniform()
+    head, _ = run.record(args.steps, args.warmup, rank, fp64_steps=args.fp64_steps)
 
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
+        es = 4
         qh = torch.tensor(np.asarray(w.q0), dtype=torch.float32).pin_memory()
         dvh = None if w.dv is None else torch.tensor(np.asarray(w.dv),
                                                      dtype=torch.float32).pin_memory()
         outh = torch.empty_like(qh).pin_memory()
-        qd, outd, dvd = tensors(torch.float32)
+        qd, outd, dvd = run.tensors(torch.float32)
         e_steps = max(10, min(200, args.steps // 10))
 
         def e2e_step():
             qd.copy_(qh, non_blocking=True)
             if dvh is not None:
                 dvd.copy_(dvh, non_blocking=True)
-            ram.step(plan, qd, outd, v0, w.dt, dv=dvd, scheme=w.scheme, nsub=nsub)
+            run.step(qd, outd, dvd)
             outh.copy_(outd, non_blocking=True)
 
         for _ in range(3):
@@ -441,7 +528,34 @@ def main():
         h2d = w.n_cells * es * (2 if w.dv is not None else 1)
         e2e = {"value": w.n_cells * world * e_steps / el / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(w.n_cells * es),
-               "steps": e_steps}
+               "steps": e_steps,
+               "note": "one step per host round trip: the host-device copies of Q (and dv) "
+                       "bound it, not the kernel"}
+        del qh, dvh, outh, qd, outd, dvd
+    run.close()
+    del run
+    torch.cuda.empty_cache()
+
+    # extra records, each with its own timing and clock sample: the batched rows
+    # (512 and 8192 uneven rows) and the large disk (the roofline case)
+    extra = {}
+    if not args.no_extra and args.workload == "disk" and disk is None:
+        for key, name, steps in (("batched", "batched", 2000),
+                                 ("batched_large", "batched_large", 300),
+                                 ("roofline_R", "disk_large", 1000)):
+            wx = _workload(name, rank)
+            rx = Runner(wx, dev, world, args)
+            if key == "roofline_R":
+                rx.refine_uniform()
+            rec, _ = rx.record(steps, args.warmup, rank, with_fp64=(key != "roofline_R"),
+                               fp64_steps=50)
+            rx.close()
+            del rx
+            torch.cuda.empty_cache()
+            if key == "batched" and world == 1:
+                rec["fp64_single_problem"] = fp64_single_problem(wx, dev)
+            extra[key] = rec
+            del wx
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -449,29 +563,23 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "rows": w.n_rows, "cells": w.n_cells,
                        "order": sorted({int(o) for o in w.order}), "limiter": w.limiter,
                        "residual": "van Leer, sub-cycled per ring" if w.dv is not None else "none",
-                       "l2": "read of 2x L2 before every timed step; step time = sum of "
-                             "per-step CUDA-event intervals",
+                       "l2": head["l2"],
                        "parallelism": "dp%d (independent disks per GPU)" % world,
-                       "tuning": tuning},
-            "gpu_launches": int(args.steps * launches_per_step(tuning)),
-            "roofline": {"bound": "hbm", "kernel": kernel_key,
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "bytes_per_cell": bpc,
-                         "traffic": None if tr is None else tr["dram_bytes_per_launch"]},
-            "fp64_single": {"value": fp64_value, "unit": UNIT, "steps": n64,
-                            "form": "the same step in FP64 (cells and arithmetic), "
-                                    "autotuned, one launch per step",
-                            "rel_l1_fp32_vs_fp64": rel},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "device_status": st,
+                       "tuning": head["tuning"]},
+            "gpu_launches": head["gpu_launches"],
+            "roofline": head["roofline"],
+            "fp64_single": head.get("fp64_same_launch"),
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": head["clocks"],
+            "device_status": head["device_status"],
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

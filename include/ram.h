@@ -89,7 +89,10 @@ typedef struct {
  * On failure *out is NULL and nothing is leaked. */
 ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_plan *out);
 
-/* Free every device and host resource of the plan.  NULL is accepted. */
+/* Free every device and host resource of the plan (the device copy of the
+ * Sec. 2 mesh, the Sec. 3.2.1 index tables and the tile lists built by
+ * ram_plan_mesh).  Host synchronous; NULL is accepted.  The caller's current
+ * device is restored before returning. */
 ram_status ram_plan_destroy(ram_plan plan);
 
 /* The shift step alone (Sec. 3, steps 1-3; Eqs. 15-18 and 26): for every row r,
@@ -119,8 +122,12 @@ ram_status ram_step(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_ou
                     double *phase, const double *v0, double dt, const void *dv_iface,
                     ram_scheme scheme, const int32_t *nsub, void *stream);
 
-/* Transpose of one linear RAM step: the plan must have RAM_LIMITER_OFF and the
- * residual scheme is donor cell.  Given the step input q_in (the same arguments
+/* Transpose of one linear RAM step (Eqs. 5-6 with the remap of Sec. 3,
+ * Eqs. 15-18 and 26).  With the limiter off the reconstruction of Sec. 3.1 /
+ * App. A is linear in Q, so the remap is a fixed matrix A(s) for a given shift
+ * and the donor-cell residual step (Eq. 6) is linear in Q too; this entry point
+ * applies the transpose of their product.  The plan must have RAM_LIMITER_OFF
+ * and the residual scheme is donor cell.  Given the step input q_in (the same arguments
  * as the forward ram_step) and the cotangent g_out of the step output, writes
  * g_in = J^T g_out and, when g_dv is not NULL, ADDS d<g_out, out>/d dv into g_dv
  * (device, same packing and dtype as dv).  At dv_j == 0 the upwind side of the
@@ -232,13 +239,18 @@ ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, v
  * refused with RAM_ERR_ARG.  Rows must have at least 512 cells and a multiple
  * of 16 bytes per row, and q_in, q_out and dv_iface must be 16-byte aligned
  * (RAM_ERR_UNSUPPORTED / RAM_ERR_ARG otherwise).
+ * flags other than RAM_LIMITER_OFF are refused with RAM_ERR_ARG.
  * Device-side conditions (CFL, non-finite shift, sub-step count) are ORed into
  * *device_errors (device int32, bits as in the plan error word: 1 CFL,
  * 2 non-finite, 4 sub-step count) when it is not NULL; the caller clears it.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current): make that first call before any stream
- * capture.  Every call overwrites the array, so calls whose kernels overlap on
- * the GPU (other streams, other threads) race; order them on one stream. */
+ * With device_errors NULL those conditions are not reported to the caller.
+ * `stream` must belong to the current device: the call uses the current
+ * device's copy of the array.  The first call on a device looks up the array's
+ * device address (once per device, with that device current) and caches it for
+ * the life of the process: make that first call before any stream capture, and
+ * do not reset the device (cudaDeviceReset) after it.  Every call overwrites
+ * the array, so calls whose kernels overlap on the GPU (other streams, other
+ * threads) race; order them on one stream. */
 ram_status ram_step_uniform_noalloc(ram_dtype dtype, int32_t n_rows, int32_t n_cells_per_row,
                                     double period, int32_t order, uint32_t flags,
                                     const void *q_in, void *q_out, const double *v0,

@@ -91,6 +91,7 @@ extern "C" ram_status ram_step_uniform_noalloc(ram_dtype dtype, int32_t n_rows,
     if (n < 512 || (n * es) % 16 != 0) return RAM_ERR_UNSUPPORTED;
     if (!(period > 0.0) || period > 1e300) return RAM_ERR_MESH;
     if (order < 2 || order > 4) return RAM_ERR_ARG;
+    if (flags & ~RAM_LIMITER_OFF) return RAM_ERR_ARG;
     if (scheme != RAM_DONOR && scheme != RAM_VANLEER) return RAM_ERR_ARG;
     if (!(dt >= 0.0) || dt > 1e300) return RAM_ERR_ARG;
     if (!q_in || !q_out || !v0) return RAM_ERR_ARG;

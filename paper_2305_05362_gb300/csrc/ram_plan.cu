@@ -299,10 +299,16 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
         return RAM_ERR_CUDA;
     int prev_dev = 0;
     cudaGetDevice(&prev_dev);
-    if (cudaSetDevice(device) != cudaSuccess) return RAM_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaSetDevice(prev_dev);
+        return RAM_ERR_CUDA;
+    }
 
     Plan *p = new (std::nothrow) Plan();
-    if (!p) return RAM_ERR_NOMEM;
+    if (!p) {
+        cudaSetDevice(prev_dev);
+        return RAM_ERR_NOMEM;
+    }
     p->device = device;
     p->n_rows = nr;
     p->n_cells = ro[nr];
@@ -322,8 +328,6 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
     std::vector<float> dx32;
     std::vector<double> dx64;
     std::vector<int32_t> buckets;
-    bool shared_uniform = false;
-    int64_t shared_mesh_off = -1;
     p->rows_h.resize(nr);
     for (int r = 0; r < nr && st == RAM_OK; ++r) {
         const int n = (int)(ro[r + 1] - ro[r]);
@@ -382,13 +386,7 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
             while (cell + 1 < n && xfix[base + cell + 1] <= start) ++cell;
             bt[b] = cell;
         }
-        if (shared) {
-            shared_uniform = false;
-            shared_mesh_off = ri.mesh_off;
-        }
     }
-    (void)shared_uniform;
-    (void)shared_mesh_off;
     if (st == RAM_OK) {
         for (int r = 0; r < nr; ++r) p->n_uniform_rows += p->rows_h[r].uniform ? 1 : 0;
         if (upload(&p->rows, p->rows_h.data(), p->rows_h.size()) != cudaSuccess ||

@@ -132,6 +132,43 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+def _need(t, name: str, numel: int, dtype=None, device=None, optional: bool = False):
+    """Refuse, before any pointer reaches the library, a tensor whose size, dtype
+    or device does not match what the C ABI will read or write through it (a short
+    buffer would be read or written past its end on the GPU)."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError("%s is required" % name)
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s has dtype %s, expected %s" % (name, t.dtype, dtype))
+    if device is not None and t.device != device:
+        raise ValueError("%s is on %s, expected %s" % (name, t.device, device))
+
+
+def _plan_device(plan: "Plan"):
+    import torch
+    return torch.device("cuda", plan.device)
+
+
+def _check_step_args(plan: "Plan", q_in, q_out, per_row=(), dv=None, nsub=None,
+                     extra_cells=()):
+    """Sizes, dtypes and devices of a planned call's tensors (ValueError)."""
+    import torch
+    dev = _plan_device(plan)
+    _need(q_in, "q_in", plan.n_cells, device=dev)
+    _dtype_code(q_in)
+    _need(q_out, "q_out", plan.n_cells, q_in.dtype, dev)
+    for name, t, optional in per_row:
+        _need(t, name, plan.n_rows, torch.float64, dev, optional)
+    _need(dv, "dv", plan.n_cells, q_in.dtype, dev, optional=True)
+    _need(nsub, "nsub", plan.n_rows, torch.int32, dev, optional=True)
+    for name, t, optional in extra_cells:
+        _need(t, name, plan.n_cells, q_in.dtype, dev, optional)
+
+
 def _stream(device: int, stream=None) -> int:
     import torch
     if stream is None:
@@ -229,6 +266,7 @@ class Plan:
 
 def shift(plan: Plan, q_in, q_out, shift_per_row, stream=None):
     """ram_shift: remap every row by +shift[r]."""
+    _check_step_args(plan, q_in, q_out, per_row=[("shift", shift_per_row, False)])
     _check(plan._lib.ram_shift(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
                                _ptr(shift_per_row), _stream(plan.device, stream)),
            "ram_shift")
@@ -237,6 +275,8 @@ def shift(plan: Plan, q_in, q_out, shift_per_row, stream=None):
 def residual_upwind(plan: Plan, q_in, q_out, dv, dt: float, scheme: int = VANLEER,
                     nsub=None, stream=None):
     """ram_residual_upwind: nsub upwind sub-steps with the interface velocity dv."""
+    _check_step_args(plan, q_in, q_out, nsub=nsub)
+    _need(dv, "dv", plan.n_cells, q_in.dtype, _plan_device(plan))
     _check(plan._lib.ram_residual_upwind(plan.handle, _dtype_code(q_in), _ptr(q_in),
                                          _ptr(q_out), _ptr(dv), float(dt), int(scheme),
                                          _ptr(nsub), _stream(plan.device, stream)),
@@ -246,6 +286,8 @@ def residual_upwind(plan: Plan, q_in, q_out, dv, dt: float, scheme: int = VANLEE
 def step(plan: Plan, q_in, q_out, v0, dt: float, dv=None, scheme: int = VANLEER,
          nsub=None, phase=None, stream=None):
     """ram_step: shift by v0*dt then the residual step (dv=None: no residual)."""
+    _check_step_args(plan, q_in, q_out, per_row=[("v0", v0, False), ("phase", phase, True)],
+                     dv=dv, nsub=nsub)
     _check(plan._lib.ram_step(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
                               _ptr(phase), _ptr(v0), float(dt), _ptr(dv), int(scheme),
                               _ptr(nsub), _stream(plan.device, stream)),
@@ -255,6 +297,8 @@ def step(plan: Plan, q_in, q_out, v0, dt: float, dv=None, scheme: int = VANLEER,
 def step_adjoint(plan: Plan, q_in, g_out, g_in, v0, dt: float, dv=None, g_dv=None,
                  nsub=None, stream=None):
     """ram_step_adjoint: g_in = J^T g_out of the linear step; adds into g_dv."""
+    _check_step_args(plan, g_out, g_in, per_row=[("v0", v0, False)], dv=dv, nsub=nsub,
+                     extra_cells=[("q_in", q_in, False), ("g_dv", g_dv, True)])
     _check(plan._lib.ram_step_adjoint(plan.handle, _dtype_code(g_out), _ptr(q_in),
                                       _ptr(g_out), _ptr(g_in), _ptr(v0), float(dt),
                                       _ptr(dv), _ptr(g_dv), _ptr(nsub),
@@ -266,6 +310,7 @@ def autotune(plan: Plan, q_in, q_out, v0, dt: float, dv=None, scheme: int = VANL
              nsub=None, reps: int = 20, stream=None) -> Tuning:
     """ram_plan_autotune: time the candidate launch shapes on these buffers and keep
     the fastest in the plan."""
+    _check_step_args(plan, q_in, q_out, per_row=[("v0", v0, False)], dv=dv, nsub=nsub)
     _check(plan._lib.ram_plan_autotune(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
                                        _ptr(v0), float(dt), _ptr(dv), int(scheme), _ptr(nsub),
                                        int(reps), _stream(plan.device, stream)),
@@ -275,6 +320,11 @@ def autotune(plan: Plan, q_in, q_out, v0, dt: float, dv=None, scheme: int = VANL
 
 def row_mass(plan: Plan, q, out, stream=None):
     """ram_row_mass: per-row mass (FP64) into out."""
+    import torch
+    dev = _plan_device(plan)
+    _need(q, "q", plan.n_cells, device=dev)
+    _dtype_code(q)
+    _need(out, "out", plan.n_rows, torch.float64, dev)
     _check(plan._lib.ram_row_mass(plan.handle, _dtype_code(q), _ptr(q), _ptr(out),
                                   _stream(plan.device, stream)), "ram_row_mass")
 
@@ -283,16 +333,34 @@ def step_uniform_noalloc(q_in, q_out, n_rows: int, period: float, order: int, v0
                          dv=None, scheme: int = VANLEER, nsub=None, limiter: bool = True,
                          device_errors=None, stream=None):
     """ram_step_uniform_noalloc: one step of n_rows equal uniform rows without any
-    device allocation (the library's static scratch array holds its tables)."""
-    lib = load()
+    device allocation (the library's static scratch array holds its tables).
+    Runs with q_in's device current, on that device's current stream unless
+    `stream` is given."""
+    import torch
+    n_rows = int(n_rows)
+    if n_rows < 1:
+        raise ValueError("n_rows must be positive")
+    if q_in.numel() % n_rows:
+        raise ValueError("q_in has %d elements, not a multiple of n_rows = %d"
+                         % (q_in.numel(), n_rows))
     n_cells = q_in.numel() // n_rows
-    dev = q_in.device.index if q_in.device.index is not None else 0
-    _check(lib.ram_step_uniform_noalloc(_dtype_code(q_in), int(n_rows), int(n_cells),
-                                        float(period), int(order),
-                                        0 if limiter else LIMITER_OFF, _ptr(q_in), _ptr(q_out),
-                                        _ptr(v0), float(dt), _ptr(dv), int(scheme), _ptr(nsub),
-                                        _ptr(device_errors), _stream(dev, stream)),
-           "ram_step_uniform_noalloc")
+    dev = q_in.device
+    _dtype_code(q_in)
+    _need(q_out, "q_out", q_in.numel(), q_in.dtype, dev)
+    _need(v0, "v0", n_rows, torch.float64, dev)
+    _need(dv, "dv", q_in.numel(), q_in.dtype, dev, optional=True)
+    _need(nsub, "nsub", n_rows, torch.int32, dev, optional=True)
+    if device_errors is not None:
+        _need(device_errors, "device_errors", 1, torch.int32, dev)
+    lib = load()
+    with torch.cuda.device(dev):
+        _check(lib.ram_step_uniform_noalloc(_dtype_code(q_in), n_rows, int(n_cells),
+                                            float(period), int(order),
+                                            0 if limiter else LIMITER_OFF, _ptr(q_in),
+                                            _ptr(q_out), _ptr(v0), float(dt), _ptr(dv),
+                                            int(scheme), _ptr(nsub), _ptr(device_errors),
+                                            _stream(dev.index, stream)),
+               "ram_step_uniform_noalloc")
 
 
 def version() -> int:

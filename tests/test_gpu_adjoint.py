@@ -49,7 +49,7 @@ def test_adjoint_matches_oracle(dtype, order):
                                              dvr[sl], w.dt, int(w.nsub[r]))
         e1 = np.abs(gi[sl] - ref_gi).sum() / np.abs(ref_gi).sum()
         e2 = np.abs(gd[sl] - ref_gd).sum() / np.abs(ref_gd).sum()
-        assert e1 <= tol and e2 <= 10 * tol, (r, e1, e2)
+        assert e1 <= tol and e2 <= tol, (r, e1, e2)
     assert plan.check_errors() == 0
 
 

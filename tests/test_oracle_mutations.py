@@ -43,6 +43,11 @@ MUTANTS = {
     "adjoint_upwind_side": ("int up = (c >= 0.0) ? cyc(j - 1, n) : j;",
                             "int up = (c >= 0.0) ? j : cyc(j - 1, n);"),
     "adjoint_plm_transpose": ("g_in[ip] += l1[i] / span;", "g_in[ip] -= l1[i] / span;"),
+    "rows_mesh_offset": ("shared_mesh ? nodes : nodes + b + r;", "shared_mesh ? nodes : nodes + b;"),
+    "rows_order_index": ("order[r], limiter, shift[r]", "order[0], limiter, shift[r]"),
+    "rows_nsub_index": ("nsub ? nsub[r] : 1", "nsub ? nsub[0] : 1"),
+    "rows_dv_offset": ("dv ? dv + b : NULL", "dv ? dv : NULL"),
+    "rows_shared_mesh_ignored": ("shared_mesh ? nodes : nodes + b + r;", "nodes + b + r;"),
 }
 
 

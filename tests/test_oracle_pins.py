@@ -542,3 +542,72 @@ def test_step_adjoint_dv_gradient_vs_finite_differences():
         e = rng.standard_normal(n)
         fd = (loss(dv + h * e) - loss(dv - h * e)) / (2 * h)
         assert fd == pytest.approx(float(gdv @ e), rel=1e-6, abs=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# the batched driver over packed rows (rows are independent, Sec. 3.5)
+# ---------------------------------------------------------------------------
+
+def _packed_rows(lens, seed, uniform=False):
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nodes = np.concatenate([wl.uniform_nodes(n) if uniform else
+                            wl.random_nodes(n, seed=seed + r, x0=0.1 * r)
+                            for r, n in enumerate(lens)])
+    return ro, nodes
+
+
+def test_step_rows_per_row_meshes_equal_single_rows():
+    """The batched driver gives, bit for bit, the single-row step of every row:
+    per-row meshes of different lengths, mixed orders, per-row shifts and
+    sub-step counts, with a residual."""
+    lens = [17, 64, 5, 230, 1, 99]
+    ro, nodes = _packed_rows(lens, 60)
+    rng = np.random.default_rng(61)
+    order = np.array([2, 3, 4, 3, 2, 4], dtype=np.int8)
+    nsub = np.array([1, 3, 2, 1, 4, 2], dtype=np.int32)
+    shifts = rng.uniform(-3, 3, len(lens))
+    q = 1.0 + rng.random(int(ro[-1]))
+    dt = 0.05
+    dv = np.concatenate([0.4 * (rng.random(n) - 0.5) * np.diff(nodes[ro[r] + r: ro[r + 1] + r + 1]).min() / dt
+                         for r, n in enumerate(lens)])
+    for limiter in (True, False):
+        got = oracle.step_rows(ro, nodes, False, order, limiter, shifts, q, dv=dv, dt=dt,
+                               scheme=oracle.VANLEER, nsub=nsub)
+        for r, n in enumerate(lens):
+            sl = slice(int(ro[r]), int(ro[r + 1]))
+            x = nodes[ro[r] + r: ro[r + 1] + r + 1]
+            ref = oracle.step(x, q[sl], shifts[r], int(order[r]), limiter, dv[sl], dt,
+                              oracle.VANLEER, int(nsub[r]))
+            assert np.array_equal(got[sl], ref), (limiter, r)
+
+
+def test_step_rows_shared_mesh_equal_single_rows():
+    """RAM_SHARED_MESH form: every row takes the first row's nodes."""
+    n, rows = 48, 5
+    x = wl.random_nodes(n, seed=62, x0=-1.0)
+    ro = np.arange(rows + 1, dtype=np.int64) * n
+    rng = np.random.default_rng(63)
+    q = 1.0 + rng.random(rows * n)
+    shifts = rng.uniform(-2, 2, rows)
+    order = np.array([3, 2, 4, 3, 2], dtype=np.int8)
+    got = oracle.step_rows(ro, x, True, order, True, shifts, q)
+    for r in range(rows):
+        sl = slice(r * n, (r + 1) * n)
+        assert np.array_equal(got[sl], oracle.step(x, q[sl], shifts[r], int(order[r]), True))
+
+
+def test_step_rows_whole_cell_rolls():
+    """Independent of the single-row driver: per-row uniform dyadic meshes of
+    different lengths, each shifted by its own whole number of cells, give the
+    cyclic permutation of each row (Sec. 1, Eq. 8) bit for bit."""
+    lens = [8, 32, 16, 64]
+    ro, nodes = _packed_rows(lens, 0, uniform=True)
+    rng = np.random.default_rng(64)
+    q = rng.random(int(ro[-1]))
+    ks = [3, -5, 16, 63]
+    shifts = np.array([k / n for k, n in zip(ks, lens)])
+    got = oracle.step_rows(ro, nodes, False, np.array([2, 3, 4, 3], dtype=np.int8), False,
+                           shifts, q)
+    for r, (n, k) in enumerate(zip(lens, ks)):
+        sl = slice(int(ro[r]), int(ro[r + 1]))
+        assert np.array_equal(got[sl], np.roll(q[sl], k)), r
