@@ -233,6 +233,9 @@ def _dominant_kernel(info, w, tuning):
     kernel the tuning selects, else the non-uniform rows' kernel."""
     if info.n_tiles_general == 0:
         return _kernel_name(tuning)
+    if tuning.get("nonuniform_kernel_f32", 0) == 1 and info.n_nseg_rows == info.n_rows - info.n_uniform_rows:
+        return "k_nseg<%s,%s>" % ("true" if w.limiter else "false",
+                                  "false" if w.dv is None else "true")
     return "k_gwarp<float>" if w.dv is None else "k_general<float>"
 
 
@@ -352,9 +355,19 @@ class Runner:
         all_seg = (info.n_uniform_rows == w.n_rows and bool(np.all(lens >= 512))
                    and bool(np.all(lens % 4 == 0))
                    and bool(np.all(np.asarray(w.row_offset) % 4 == 0)))
-        own = all_seg and t["uniform_kernel_f32"] == 1 and t["seg_variant_f32"] == 2
-        general = {int(o) for o, n in zip(w.order, lens)} if info.n_tiles_general else set()
-        return (0 if own else 1) + len(uniform_orders) + len(general)
+        nonuni = w.n_rows - info.n_uniform_rows
+        nseg = t.get("nonuniform_kernel_f32", 0) == 1 and nonuni > 0
+        nseg_all = nseg and info.n_nseg_rows == nonuni
+        own = ((info.n_uniform_rows == 0 or
+                (all_seg and t["uniform_kernel_f32"] == 1 and t["seg_variant_f32"] == 2))
+               and (nonuni == 0 or nseg_all))
+        if nseg_all:
+            general = 1
+        else:
+            orders = {int(o) for o in w.order} if info.n_tiles_general else set()
+            per_order = 1 if w.dv is None else 2  # the tiled kernel: whole-row and windowed
+            general = (1 if nseg else 0) + per_order * len(orders)
+        return (0 if own else 1) + len(uniform_orders) + general
 
     def record(self, steps, warmup, rank, with_fp64=True, fp64_steps=50):
         """Timed FP32 run with its clock sample and roofline; the FP64 form of the

@@ -170,6 +170,8 @@ typedef struct {
     int32_t tile_cells;       /* output cells per tile */
     int32_t threads;          /* threads per CTA */
     int32_t device;
+    int32_t n_nseg_rows;      /* rows with their own mesh that FP32 steps run on the
+                                 warp-segment kernel (the others take the tiled one) */
 } ram_plan_info;
 
 ram_status ram_plan_query(ram_plan plan, ram_plan_info *info);
@@ -202,6 +204,11 @@ typedef struct {
                                            the default) */
     int32_t seg_warps;                  /* warp-segment kernel: warps per row CTA, 3..8
                                            (default 3) */
+    int32_t nonuniform_kernel_f32;      /* FP32 rows with their own mesh: 0 = the
+                                           per-order kernels (shared-memory-free without
+                                           a residual, tiled with one; the default),
+                                           1 = the warp-segment kernel (one launch for
+                                           every order, shift and residual together) */
 } ram_tuning;
 
 ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out);
@@ -216,8 +223,9 @@ ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *tuning);
  * for FP32 the streaming-warp kernel with 4 or 8 cells per lane, and the
  * persistent whole-row kernel with (cells per thread, CTAs per SM) in
  * {5,7,9,11,15} x {2,3,4} as the register budget allows; tile cells
- * {256,512,1024,2048} x threads {128,256,512} of the tiled kernels.  Host
- * synchronous; overwrites q_out. */
+ * {256,512,1024,2048} x threads {128,256,512} of the tiled kernels; for FP32
+ * rows with their own mesh, the warp-segment kernel against the per-order
+ * kernels.  Host synchronous; overwrites q_out. */
 ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
                              const double *v0, double dt, const void *dv_iface,
                              ram_scheme scheme, const int32_t *nsub, int32_t reps,

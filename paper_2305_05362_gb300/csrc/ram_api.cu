@@ -63,17 +63,21 @@ StepArgs base_args(const Plan *p, const void *q_in, void *q_out)
     return a;
 }
 
-// Every row of the plan is an FP32 warp-segment row and this launch runs them with
-// the shared-memory ring kernel (which needs 16-byte aligned arrays), which forms
-// the shift parameters itself: no parameter kernel is needed.
+// Every row of this FP32 launch forms its own shift parameters, so no parameter
+// kernel is needed: uniform rows on the shared-memory ring form of the
+// warp-segment kernel (which needs 16-byte aligned arrays), rows with their own
+// mesh on the non-uniform warp-segment kernel.
 bool rows_form_params(const Plan &p, ram_dtype dt, const StepArgs &a)
 {
-    if (dt != RAM_F32 || p.uniform_kernel[0] != 1 || p.seg_variant != 2) return false;
-    for (const void *ptr : {a.q_in, static_cast<const void *>(a.q_out), a.dv})
-        if ((uintptr_t)ptr % 16) return false;
+    if (dt != RAM_F32) return false;
     size_t seg = 0;
-    for (int o = 2; o <= 4; ++o) seg += p.rows_seg_h[0][o].size();
-    return seg == (size_t)p.n_rows;
+    if (p.n_uniform_rows > 0) {
+        if (p.uniform_kernel[0] != 1 || p.seg_variant != 2) return false;
+        for (const void *ptr : {a.q_in, static_cast<const void *>(a.q_out), a.dv})
+            if ((uintptr_t)ptr % 16) return false;
+        for (int o = 2; o <= 4; ++o) seg += p.rows_seg_h[0][o].size();
+    }
+    return seg + (size_t)(p.nu_kernel == 1 ? p.nseg_rows : 0) == (size_t)p.n_rows;
 }
 
 ram_status run(const Plan *p, ram_dtype dt, const StepArgs &a0, void *stream)

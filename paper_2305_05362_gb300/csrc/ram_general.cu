@@ -630,9 +630,27 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+// A list of non-uniform tiles of one order for the general kernels: every row's
+// (FP64) or the rows the FP32 warp-segment kernel does not take.
+struct GenList {
+    const Tile *tiles;
+    int n, whole;
+    const int32_t *wcap, *qcap;  // [2]: whole-row and windowed classes
+};
+
+GenList gen_list(const Plan &p, int order, bool f32)
+{
+    if (f32 && p.nu_kernel == 1)
+        return {p.tiles_general32[order], (int)p.tiles_general32_h[order].size(),
+                p.gen32_whole[order], p.gen32_wcap[order], p.gen32_qcap[order]};
+    return {p.tiles_general[order], (int)p.tiles_general_h[order].size(), p.gen_whole[order],
+            p.gen_wcap[order], p.gen_qcap[order]};
+}
+
 template <typename T, int ORDER>
-cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t s, int first,
-                                 int count, int wcap, int qcap, int &launched)
+cudaError_t launch_general_class(const Plan &p, const GenList &gl, const StepArgs &a0,
+                                 cudaStream_t s, int first, int count, int wcap, int qcap,
+                                 int &launched)
 {
     if (count == 0) return cudaSuccess;
     const bool resid = a0.mode != MODE_SHIFT && a0.dv != nullptr;
@@ -648,7 +666,7 @@ cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t
         configured[dev] = smem;
     }
     StepArgs a = a0;
-    a.tiles = p.tiles_general[ORDER] + first;
+    a.tiles = gl.tiles + first;
     a.n_tiles = count;
     // the plan's threads per CTA (every phase of a tile strides over its cells)
     const int threads = p.threads < 512 ? p.threads : 512;
@@ -664,12 +682,13 @@ cudaError_t launch_general_class(const Plan &p, const StepArgs &a0, cudaStream_t
 template <typename T, int ORDER>
 cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, int &launched)
 {
-    const int n = (int)p.tiles_general_h[ORDER].size();
+    const GenList gl = gen_list(p, ORDER, sizeof(T) == 4);
+    const int n = gl.n;
     if (n == 0) return cudaSuccess;
     if (a0.mode == MODE_SHIFT || a0.dv == nullptr) {
         // no residual: the shared-memory-free kernel takes every tile in one launch
         StepArgs a = a0;
-        a.tiles = p.tiles_general[ORDER];
+        a.tiles = gl.tiles;
         a.n_tiles = n;
         const int threads = p.threads < 512 ? p.threads : 512;
         cudaError_t e = launch_pdl(k_gwarp<T, ORDER, 2>, n, threads, 0, s, a,
@@ -678,12 +697,12 @@ cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, 
         if (e == cudaSuccess) ++launched;
         return e;
     }
-    const int nw = p.gen_whole[ORDER];
-    cudaError_t e = launch_general_class<T, ORDER>(p, a0, s, 0, nw, p.gen_wcap[0][ORDER],
-                                                   p.gen_qcap[0][ORDER], launched);
+    const int nw = gl.whole;
+    cudaError_t e = launch_general_class<T, ORDER>(p, gl, a0, s, 0, nw, gl.wcap[0], gl.qcap[0],
+                                                   launched);
     if (e != cudaSuccess) return e;
-    return launch_general_class<T, ORDER>(p, a0, s, nw, n - nw, p.gen_wcap[1][ORDER],
-                                          p.gen_qcap[1][ORDER], launched);
+    return launch_general_class<T, ORDER>(p, gl, a0, s, nw, n - nw, gl.wcap[1], gl.qcap[1],
+                                          launched);
 }
 
 // ---------------- per-row mass (Eq. 10) ----------------
@@ -720,6 +739,9 @@ cudaError_t launch_general(const Plan &p, ram_dtype dt, const StepArgs &a, cudaS
     cudaError_t e = cudaSuccess;
     int launched = 0;  // general launches so far in this step
     if (dt == RAM_F32) {
+        // rows with their own mesh: the warp-segment kernel, then the rows it does
+        // not take on the general kernels
+        if (p.nu_kernel == 1 && (e = launch_nseg(p, a, s)) != cudaSuccess) return e;
         if ((e = launch_general_t<float, 2>(p, a, s, launched)) != cudaSuccess) return e;
         if ((e = launch_general_t<float, 3>(p, a, s, launched)) != cudaSuccess) return e;
         return launch_general_t<float, 4>(p, a, s, launched);

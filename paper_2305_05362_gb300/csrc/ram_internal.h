@@ -30,6 +30,9 @@ struct RowInfo {
     int32_t order;        // 2, 3, 4
     int32_t uniform;      // 1: equal widths, O(1) edge index
     int32_t bucket_bits;  // log2 of the row's bucket count
+    int32_t qshift;       // FP32 warp-segment kernel: window-relative fixed-point
+                          // positions are kept as 32-bit values in units of 2^qshift
+    int32_t pad;
     double period;        // L
     double cells_per_length;  // N / L
     double dx;            // L / N (uniform rows)
@@ -55,6 +58,18 @@ struct Tile {
 // reconstruction halo (cells per side) of the general kernel.
 constexpr int kGenHalo = 2 * RAM_MAX_NSUB;
 constexpr int kGenHR = 2;
+
+// FP32 rows with their own mesh: the warp-segment kernel (ram_nseg.cu).  A lane
+// forms the reconstructions of kNsegV consecutive window cells; a segment has
+// at most kNseg output cells; a CTA of kNsegWarps warps takes a tile of up to
+// kNsegWarps * kNsegPerWarp segments.
+constexpr int kNsegV = 4;
+constexpr int kNseg = 96;
+constexpr int kNsegHR = 2;          // reconstruction halo, cells per side
+constexpr int kNsegWarps = 8;
+constexpr int kNsegPerWarp = 2;
+// shortest row it takes (a segment and its residual halo span less than a period)
+constexpr int kNsegMinCells = 2 * kGenHalo + 2;
 
 // Tries of a bounded device-side wait before it gives up and records a timeout.
 constexpr uint32_t kWaitLimit = 1u << 20;
@@ -119,8 +134,18 @@ struct Plan {
     // per order: whole-row tiles, and for (whole-row, windowed) tiles the largest
     // source window and output extent (cells) the general kernel stages
     int32_t gen_whole[5] = {0};
-    int32_t gen_wcap[2][5] = {{0}};
-    int32_t gen_qcap[2][5] = {{0}};
+    int32_t gen_wcap[5][2] = {{0}};  // [order][class]
+    int32_t gen_qcap[5][2] = {{0}};
+    // FP32: the tiles of the rows the warp-segment kernel does not take (the same
+    // layout as above), and the warp-segment kernel's tiles (window = cells per
+    // segment of the row) with the largest source window of any of its segments
+    std::vector<Tile> tiles_general32_h[5];
+    int32_t gen32_whole[5] = {0};
+    int32_t gen32_wcap[5][2] = {{0}};
+    int32_t gen32_qcap[5][2] = {{0}};
+    std::vector<Tile> tiles_nseg_h;
+    int32_t nseg_rows = 0;
+    int32_t nu_kernel = 0;         // FP32 rows with their own mesh: 1 = warp-segment kernel
     // uniform rows taken by the persistent whole-row kernel, per dtype and order, and
     // the tiles of the remaining uniform rows
     std::vector<int32_t> rows_fit_h[2][5];
@@ -147,6 +172,8 @@ struct Plan {
     RowInfo *rows = nullptr;
     Tile *tiles_uniform[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     Tile *tiles_general[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    Tile *tiles_general32[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    Tile *tiles_nseg = nullptr;
     int32_t *rows_fit[2][5] = {{nullptr}};
     RowPos *rows_fit_pos[2][5] = {{nullptr}};
     Tile *tiles_rest[2][5] = {{nullptr}};
@@ -186,6 +213,12 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // launchers (ram_uniform.cu, ram_general.cu)
 cudaError_t launch_uniform(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_general(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s);
+// FP32 rows with their own mesh, warp-segment kernel (ram_nseg.cu)
+cudaError_t launch_nseg(const Plan &p, const StepArgs &a, cudaStream_t s);
+size_t nseg_smem_bytes(bool resid);
+// largest source window (cells) a warp of it stages; rows above it take the tiled
+// kernels
+int nseg_window_cap();
 cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *out,
                             cudaStream_t s);
 cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,

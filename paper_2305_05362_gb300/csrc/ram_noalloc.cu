@@ -60,6 +60,8 @@ __global__ void k_static_rows(RowInfo *rows, int32_t *ids, int n_rows, int n, do
     ri.order = order;
     ri.uniform = 1;
     ri.bucket_bits = 0;
+    ri.qshift = 0;
+    ri.pad = 0;
     ri.period = period;
     ri.cells_per_length = (double)n / period;
     ri.dx = period / n;

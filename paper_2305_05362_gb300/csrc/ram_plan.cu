@@ -70,10 +70,13 @@ cudaError_t upload(T **dst, const T *src, size_t count)
 
 void free_lists(Plan &p)
 {
+    cudaFree(p.tiles_nseg);
+    p.tiles_nseg = nullptr;
     for (int o = 0; o < 5; ++o) {
         cudaFree(p.tiles_uniform[o]);
         cudaFree(p.tiles_general[o]);
-        p.tiles_uniform[o] = p.tiles_general[o] = nullptr;
+        cudaFree(p.tiles_general32[o]);
+        p.tiles_uniform[o] = p.tiles_general[o] = p.tiles_general32[o] = nullptr;
         for (int d = 0; d < 2; ++d) {
             cudaFree(p.rows_fit[d][o]);
             cudaFree(p.rows_fit_pos[d][o]);
@@ -108,6 +111,82 @@ void free_device(Plan &p)
     p.err = nullptr;
 }
 
+// Widths of a row twice over (cyclic sums without index wraps).
+std::vector<double> doubled_widths(const double *x, int n)
+{
+    std::vector<double> w2(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) w2[i] = w2[i + n] = x[i + 1] - x[i];
+    return w2;
+}
+
+// The longest physical extent of `span` consecutive cells (cyclic), and the most
+// source cells an interval that long can touch, over every placement: for every
+// start st, cells st..e-1 fit strictly inside it; it also touches cell e and the
+// cell st-1 it may start in.
+int most_cells_touched(const std::vector<double> &w2, int n, int span)
+{
+    double len_max = 0.0, acc = 0.0;
+    for (int k = 0; k < span; ++k) acc += w2[k % (2 * n)];
+    len_max = acc;
+    for (int st = 1; st < n; ++st) {
+        acc += w2[(st + span - 1) % (2 * n)] - w2[st - 1];
+        len_max = std::max(len_max, acc);
+    }
+    int best = 0;
+    acc = 0.0;
+    int e = 0;
+    for (int st = 0; st < n; ++st) {
+        if (e < st) {
+            e = st;
+            acc = 0.0;
+        }
+        while (e < st + n && acc + w2[e] < len_max) acc += w2[e++];
+        best = std::max(best, e - st + 2);
+        if (e > st) acc -= w2[st];
+    }
+    return std::min(best, n + 1);
+}
+
+// Units (a power of two of fixed-point length, 2^qs) in which the FP32
+// warp-segment kernel keeps window-relative positions as 32-bit values: every
+// window of up to `wb` cells must span less than 2^31 units, and every cell at
+// least 2^21 (so that in-cell offsets keep about 21 significant bits); -1 when
+// the row's widths vary too much for both.
+int position_shift(const std::vector<double> &w2, int n, int wb, double L)
+{
+    double acc = 0.0, len_max = 0.0, w_min = w2[0];
+    for (int k = 0; k < wb; ++k) acc += w2[k % (2 * n)];
+    len_max = acc;
+    for (int st = 1; st < n; ++st) {
+        acc += w2[(st + wb - 1) % (2 * n)] - w2[st - 1];
+        len_max = std::max(len_max, acc);
+    }
+    for (int i = 0; i < n; ++i) w_min = std::min(w_min, w2[i]);
+    const double two64 = 18446744073709551616.0;
+    const double lfix = std::min(len_max / L, 1.0) * two64;
+    int qs = std::max(0, (int)std::floor(std::log2(lfix)) - 30);
+    if (std::ldexp(lfix, -qs) >= 2147483648.0) ++qs;
+    if (std::ldexp(w_min / L * two64, -qs) < 2097152.0) return -1;
+    return qs;
+}
+
+// The general kernels' per-order launch shapes of a tile list: whole-row tiles
+// (window 0) first, and for each class the largest window and output extent.
+void general_caps(const Plan &p, std::vector<Tile> &tl, int32_t &whole, int32_t wcap[2],
+                  int32_t qcap[2])
+{
+    std::stable_partition(tl.begin(), tl.end(), [](const Tile &t) { return t.window == 0; });
+    whole = 0;
+    for (int c = 0; c < 2; ++c) wcap[c] = qcap[c] = 0;
+    for (const Tile &t : tl) {
+        const int c = t.window == 0 ? 0 : 1;
+        if (c == 0) ++whole;
+        const int w = c == 0 ? p.rows_h[t.row].n + 2 * kGenHR : t.window;
+        wcap[c] = std::max(wcap[c], w);
+        qcap[c] = std::max(qcap[c], t.count + 2 * kGenHalo);
+    }
+}
+
 }  // namespace
 
 // Split every row into near-equal tiles of at most tile_cells output cells and
@@ -117,9 +196,12 @@ void free_device(Plan &p)
 ram_status build_tiles(Plan &p)
 {
     free_lists(p);
+    p.tiles_nseg_h.clear();
+    p.nseg_rows = 0;
     for (int o = 0; o < 5; ++o) {
         p.tiles_uniform_h[o].clear();
         p.tiles_general_h[o].clear();
+        p.tiles_general32_h[o].clear();
         for (int d = 0; d < 2; ++d) {
             p.rows_fit_h[d][o].clear();
             p.rows_fit_pos_h[d][o].clear();
@@ -182,15 +264,51 @@ ram_status build_tiles(Plan &p)
             }
             continue;
         }
+        const double *x = (p.flags & RAM_SHARED_MESH) ? p.nodes_h.data()
+                                                       : p.nodes_h.data() + p.row_offset[r] + r;
+        const std::vector<double> w2 = doubled_widths(x, n);
+        // FP32: the warp-segment kernel, with segments short enough that a segment
+        // and its largest residual halo span less than a period, and a source
+        // window that fits its shared-memory region
+        bool nseg = false;
+        p.rows_h[r].qshift = 0;
+        if (n >= kNsegMinCells) {
+            // the longest segment whose source window, residual halo included, fits
+            // the warp's window; preferably one whose window without a residual
+            // fits half of it (one pass of the reconstruction)
+            const int cap = nseg_window_cap();
+            const int seg_max = std::min(kNseg, n - 1 - 2 * kGenHalo);
+            int seg = 0, wb = 0;
+            for (int pass = 0; pass < 2 && seg == 0; ++pass) {
+                for (int sg = seg_max; sg >= 1; sg -= (sg > 8 ? 8 : sg)) {
+                    const int w1 = most_cells_touched(w2, n, sg + 2 * kGenHalo) + 2 * kNsegHR + 1;
+                    const int w0 = most_cells_touched(w2, n, sg) + 2 * kNsegHR + 1;
+                    if (w1 <= cap && (pass == 1 || w0 <= cap / 2)) {
+                        seg = sg;
+                        wb = w1;
+                        break;
+                    }
+                    if (sg < kNseg / 3) break;
+                }
+            }
+            int qs = -1;
+            if (seg > 0) qs = position_shift(w2, n, wb, x[n] - x[0]);
+            if (qs >= 0) {
+                nseg = true;
+                ++p.nseg_rows;
+                p.rows_h[r].qshift = qs;
+                const int per_tile = seg * kNsegWarps * kNsegPerWarp;
+                for (int a = 0; a < n; a += per_tile)
+                    p.tiles_nseg_h.push_back(Tile{r, a, std::min(per_tile, n - a), seg});
+            }
+        }
+        std::vector<Tile> &g32 = p.tiles_general32_h[ri.order];
         // non-uniform row: one cyclic tile for short rows, else windowed tiles
         if (n <= 2 * tg + 4 * halo_res) {
             p.tiles_general_h[ri.order].push_back(Tile{r, 0, n, 0});
+            if (!nseg) g32.push_back(Tile{r, 0, n, 0});
             continue;
         }
-        const double *x = (p.flags & RAM_SHARED_MESH) ? p.nodes_h.data()
-                                                       : p.nodes_h.data() + p.row_offset[r] + r;
-        std::vector<double> w2(2 * (size_t)n);
-        for (int i = 0; i < n; ++i) w2[i] = w2[i + n] = x[i + 1] - x[i];
         const int nt = (n + tg - 1) / tg;
         // the longest physical extent of a tile's output cells with their halo,
         // [a - halo, b + halo) (cyclic), bounds the source cells of every tile
@@ -226,22 +344,30 @@ ram_status build_tiles(Plan &p)
             const int a = (int)((int64_t)n * t / nt);
             const int b = (int)((int64_t)n * (t + 1) / nt);
             p.tiles_general_h[ri.order].push_back(Tile{r, a, b - a, window});
+            if (!nseg) g32.push_back(Tile{r, a, b - a, window});
         }
     }
+    // tiles of one reconstruction order next to each other: CTAs that run at the
+    // same time mostly run the same code
+    std::stable_sort(p.tiles_nseg_h.begin(), p.tiles_nseg_h.end(),
+                     [&p](const Tile &a, const Tile &b) {
+                         return p.rows_h[a.row].order < p.rows_h[b.row].order;
+                     });
+    if (upload(&p.tiles_nseg, p.tiles_nseg_h.data(), p.tiles_nseg_h.size()) != cudaSuccess)
+        return RAM_ERR_NOMEM;
+    // the rows' position units (qshift) live in the device row table
+    if (p.rows && cudaMemcpy(p.rows, p.rows_h.data(), sizeof(RowInfo) * p.rows_h.size(),
+                             cudaMemcpyHostToDevice) != cudaSuccess)
+        return RAM_ERR_CUDA;
     for (int o = 2; o <= 4; ++o) {
         // the general kernel runs whole-row tiles (window 0) and windowed tiles as
         // two launches, each with the shared memory its own largest tile needs
-        std::vector<Tile> &tg_o = p.tiles_general_h[o];
-        std::stable_partition(tg_o.begin(), tg_o.end(), [](const Tile &t) { return t.window == 0; });
-        p.gen_whole[o] = 0;
-        for (int c = 0; c < 2; ++c) p.gen_wcap[c][o] = p.gen_qcap[c][o] = 0;
-        for (const Tile &t : tg_o) {
-            const int c = t.window == 0 ? 0 : 1;
-            if (c == 0) ++p.gen_whole[o];
-            const int w = c == 0 ? p.rows_h[t.row].n + 2 * kGenHR : t.window;
-            p.gen_wcap[c][o] = std::max(p.gen_wcap[c][o], w);
-            p.gen_qcap[c][o] = std::max(p.gen_qcap[c][o], t.count + 2 * kGenHalo);
-        }
+        general_caps(p, p.tiles_general_h[o], p.gen_whole[o], p.gen_wcap[o], p.gen_qcap[o]);
+        general_caps(p, p.tiles_general32_h[o], p.gen32_whole[o], p.gen32_wcap[o],
+                     p.gen32_qcap[o]);
+        if (upload(&p.tiles_general32[o], p.tiles_general32_h[o].data(),
+                   p.tiles_general32_h[o].size()) != cudaSuccess)
+            return RAM_ERR_NOMEM;
         if (upload(&p.tiles_uniform[o], p.tiles_uniform_h[o].data(),
                    p.tiles_uniform_h[o].size()) != cudaSuccess)
             return RAM_ERR_NOMEM;
@@ -442,6 +568,7 @@ extern "C" ram_status ram_plan_query(ram_plan plan, ram_plan_info *info)
     info->tile_cells = p->tile_cells;
     info->threads = p->threads;
     info->device = p->device;
+    info->n_nseg_rows = p->nseg_rows;
     return RAM_OK;
 }
 

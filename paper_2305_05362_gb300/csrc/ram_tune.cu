@@ -46,6 +46,7 @@ extern "C" ram_status ram_plan_get_tuning(ram_plan plan, ram_tuning *out)
     out->stream_cells_per_lane_f32 = p->stream_v;
     out->seg_variant_f32 = p->seg_variant;
     out->seg_warps = p->seg_warps;
+    out->nonuniform_kernel_f32 = p->nu_kernel;
     return RAM_OK;
 }
 
@@ -62,6 +63,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     if (!sv) return RAM_ERR_ARG;
     if (t->seg_variant_f32 < 0 || t->seg_variant_f32 > 2) return RAM_ERR_ARG;
     if (t->seg_warps < 3 || t->seg_warps > 8) return RAM_ERR_ARG;
+    if (t->nonuniform_kernel_f32 != 0 && t->nonuniform_kernel_f32 != 1) return RAM_ERR_ARG;
     if (t->rows_ctas_per_sm_f32 < 1 || t->rows_ctas_per_sm_f32 > 4 || t->rows_ctas_per_sm_f64 != 1)
         return RAM_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(plan);
@@ -78,6 +80,7 @@ extern "C" ram_status ram_plan_set_tuning(ram_plan plan, const ram_tuning *t)
     p->stream_v = t->stream_cells_per_lane_f32;
     p->seg_variant = t->seg_variant_f32;
     p->seg_warps = t->seg_warps;
+    p->nu_kernel = t->nonuniform_kernel_f32;
     return RAM_OK;
 }
 
@@ -200,6 +203,21 @@ extern "C" ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const vo
             }
         ram_status r = ram_plan_set_tiling(plan, best_tc, best_th);
         if (st == RAM_OK) st = r;
+    }
+    if (d == 0 && p->nseg_rows > 0 && st == RAM_OK) {
+        // FP32 rows with their own mesh: the warp-segment kernel or the per-order ones
+        int best_nu = p->nu_kernel;
+        float best = 3.4e38f;
+        for (int nu = 1; nu >= 0 && st == RAM_OK; --nu) {
+            p->nu_kernel = nu;
+            float ms = 0;
+            st = time_once(&ms);
+            if (st == RAM_OK && ms < best) {
+                best = ms;
+                best_nu = nu;
+            }
+        }
+        p->nu_kernel = best_nu;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

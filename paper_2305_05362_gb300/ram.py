@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int32), ("n_cells", ctypes.c_int64),
                 ("n_uniform_rows", ctypes.c_int32), ("n_tiles_uniform", ctypes.c_int32),
                 ("n_tiles_general", ctypes.c_int32), ("tile_cells", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("n_nseg_rows", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -63,7 +64,8 @@ class Tuning(ctypes.Structure):
                 ("uniform_kernel_f32", ctypes.c_int32), ("uniform_kernel_f64", ctypes.c_int32),
                 ("rows_ctas_per_sm_f32", ctypes.c_int32), ("rows_ctas_per_sm_f64", ctypes.c_int32),
                 ("stream_cells_per_lane_f32", ctypes.c_int32),
-                ("seg_variant_f32", ctypes.c_int32), ("seg_warps", ctypes.c_int32)]
+                ("seg_variant_f32", ctypes.c_int32), ("seg_warps", ctypes.c_int32),
+                ("nonuniform_kernel_f32", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -48,8 +48,9 @@ def batched_512():
     return wl.batched(n_rows=512)
 
 
-@pytest.mark.parametrize("dtype", ["float32", "float64"])
-def test_batched_512_rows_autotuned(batched_512, dtype):
+@pytest.mark.parametrize("dtype,nseg", [("float32", None), ("float32", 1), ("float64", None)])
+def test_batched_512_rows_autotuned(batched_512, dtype, nseg):
+    """Autotuned launch shapes (nseg None), and the FP32 warp-segment kernel forced."""
     w = batched_512
     assert int(np.diff(w.row_offset).max()) > 60000
     plan = ram.Plan.from_workload(w)
@@ -57,6 +58,11 @@ def test_batched_512_rows_autotuned(batched_512, dtype):
     out = torch.empty_like(q)
     v0 = _t(w.v0, torch.float64)
     ram.autotune(plan, q, out, v0, w.dt, reps=3)
+    if nseg is not None:
+        t = plan.tuning()
+        t.nonuniform_kernel_f32 = nseg
+        plan.set_tuning(t)
+        assert plan.info().n_nseg_rows == w.n_rows
     ram.step(plan, q, out, v0, w.dt)
     torch.cuda.synchronize()
     assert plan.check_errors() == 0

@@ -20,20 +20,30 @@ def _t(a, dtype):
     return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
 
 
+def _use_nseg(plan, on=True):
+    """Select the FP32 warp-segment kernel for the plan's rows with their own mesh
+    (the default is the per-order kernels)."""
+    t = plan.tuning()
+    t.nonuniform_kernel_f32 = 1 if on else 0
+    plan.set_tuning(t)
+    return plan
+
+
 def _rounded(a, dtype):
     a = np.asarray(a, dtype=np.float64)
     return a.astype(np.float32).astype(np.float64) if dtype == "float32" else a
 
 
-@pytest.mark.parametrize("dtype", ["float64", "float32"])
-def test_line_nonuniform_c2(dtype):
+@pytest.mark.parametrize("dtype,nseg", [("float64", False), ("float32", False),
+                                        ("float32", True)])
+def test_line_nonuniform_c2(dtype, nseg):
     """4096 cells, log-uniform widths in [0.5, 2] x mean, three Gaussians, 40.7 mean
     cells per step, dv = 0.05 sin(4 pi x), PPM + van Leer, the recipe's 1000 steps.
     At steps 1, 10, 100 and 1000: the GPU step against the oracle step from the
     same (GPU) input, and the whole GPU trajectory against the FP64 oracle's own
     trajectory, both at the stated tolerance."""
     w = wl.line_nonuniform()
-    plan = ram.Plan.from_workload(w)
+    plan = _use_nseg(ram.Plan.from_workload(w), nseg)
     assert plan.info().n_uniform_rows == 0
     q = _t(w.q0, DT[dtype])
     buf = torch.empty_like(q)
@@ -152,14 +162,15 @@ def test_mixed_uniform_and_nonuniform_rows(dtype):
         assert err <= TOL[dtype], (r, err)
 
 
-@pytest.mark.parametrize("dtype", ["float32", "float64"])
-def test_batched_uneven_rows(dtype):
+@pytest.mark.parametrize("dtype,nseg", [("float32", False), ("float32", True),
+                                        ("float64", False)])
+def test_batched_uneven_rows(dtype, nseg):
     """The batched recipe (uneven rows with their own meshes, per-row shifts of
     0.3-200 mean cells, orders 2/3/4, limiter off), reduced to 40 rows of up to 8192
     cells, 20 steps: at steps 1, 5 and 20 the step from the GPU's own input and the
     trajectory against the FP64 oracle's, both at the stated tolerance."""
     w = wl.batched(n_rows=40, n_max=8192, steps=20)
-    plan = ram.Plan.from_workload(w)
+    plan = _use_nseg(ram.Plan.from_workload(w), nseg)
     q = _t(w.q0, DT[dtype])
     buf = torch.empty_like(q)
     v0 = _t(w.v0, torch.float64)
@@ -215,3 +226,80 @@ def test_step_conserves_mass_fp64():
     torch.cuda.synchronize()
     rel = ((m1 - m0).abs() / m0.abs()).max().item()
     assert rel <= 1e-13, rel
+
+
+@pytest.mark.parametrize("n", [34, 35, 64, 127, 129, 300, 2049, 5000, 40000])
+@pytest.mark.parametrize("order,limiter", [(2, True), (2, False), (3, True), (3, False),
+                                           (4, False)])
+def test_fp32_warp_segment_rows(n, order, limiter):
+    """FP32 rows with their own mesh on the warp-segment kernel: rows from the
+    shortest it takes to many tiles, shifts of many periods both ways, shift alone
+    and with donor / van Leer residuals of 1..8 sub-steps (the widest halo)."""
+    x = wl.random_nodes(n, seed=3 * n + order, ratio=4.0, x0=0.3)
+    plan = _use_nseg(ram.Plan([0, n], x, order=order, limiter=limiter))
+    assert plan.info().n_nseg_rows == 1
+    rng = np.random.default_rng(n + order)
+    q0 = _rounded(1.0 + rng.random(n), "float32")
+    dxmin = np.diff(x).min()
+    dt = 0.1
+    qd = _t(q0, torch.float32)
+    out = torch.empty_like(qd)
+    for s in (0.0, 0.3 * dxmin, 0.4321, 7.77, -3.1415):
+        ram.shift(plan, qd, out, _t([s], torch.float64))
+        torch.cuda.synchronize()
+        ref = oracle.shift(x, q0, s, order, limiter)
+        err = np.sum(np.abs(out.double().cpu().numpy() - ref) * np.diff(x)) / np.sum(np.abs(ref) * np.diff(x))
+        assert err <= TOL["float32"], ("shift", s, err)
+    for scheme, nsub in ((ram.DONOR, 1), (ram.VANLEER, 1), (ram.VANLEER, 8), (ram.DONOR, 5)):
+        dv = _rounded((rng.random(n) - 0.5) * 1.6 * nsub * dxmin / dt, "float32")
+        v0 = _t([7.3 * (1.0 - x[0]) / dt], torch.float64)
+        ram.step(plan, qd, out, v0, dt, dv=_t(dv, torch.float32), scheme=scheme,
+                 nsub=_t([nsub], torch.int32))
+        torch.cuda.synchronize()
+        ref = oracle.step(x, q0, oracle.shift_from_velocity(v0.item(), dt), order, limiter, dv, dt,
+                          scheme, nsub)
+        err = np.sum(np.abs(out.double().cpu().numpy() - ref) * np.diff(x)) / np.sum(np.abs(ref) * np.diff(x))
+        assert err <= TOL["float32"], (scheme, nsub, err)
+    assert plan.check_errors() == 0
+
+
+def test_fp32_warp_segment_full_period_and_zero_shift_bit_exact():
+    """Whole periods and a zero shift return the input bit for bit on the FP32
+    warp-segment kernel (every shifted edge on its own node: the exact-cover copy)."""
+    for n in (34, 600, 3000, 70000):
+        x = wl.random_nodes(n, seed=n + 1)
+        plan = _use_nseg(ram.Plan([0, n], x, order=3))
+        assert plan.info().n_nseg_rows == 1
+        q = torch.rand(n, dtype=torch.float32, device=DEV) + 0.5
+        out = torch.empty_like(q)
+        for m in (0.0, 1.0, 3.0, -2.0):
+            ram.shift(plan, q, out, _t([m], torch.float64))
+            torch.cuda.synchronize()
+            assert torch.equal(out, q), (n, m)
+
+
+def test_fp32_rows_the_warp_segment_kernel_does_not_take():
+    """Rows shorter than its minimum or with a source window above its cap run the
+    tiled kernels in the same FP32 step; every row matches the oracle."""
+    lens = [5, 33, 34, 2000, 1500]
+    ratios = [4.0, 4.0, 4.0, 4.0, 4000.0]
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nodes = np.concatenate([wl.random_nodes(n, seed=40 + r, ratio=ra)
+                            for r, (n, ra) in enumerate(zip(lens, ratios))])
+    plan = _use_nseg(ram.Plan(ro, nodes, order=3))
+    assert plan.info().n_nseg_rows == 2 or plan.info().n_nseg_rows == 3
+    rng = np.random.default_rng(41)
+    q0 = _rounded(1.0 + rng.random(int(ro[-1])), "float32")
+    v0 = rng.uniform(-3, 3, len(lens))
+    qd = _t(q0, torch.float32)
+    out = torch.empty_like(qd)
+    ram.step(plan, qd, out, _t(v0, torch.float64), 1.0)
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    for r in range(len(lens)):
+        sl = slice(int(ro[r]), int(ro[r + 1]))
+        x = nodes[ro[r] + r: ro[r + 1] + r + 1]
+        ref = oracle.step(x, q0[sl], oracle.shift_from_velocity(v0[r], 1.0), 3, True)
+        err = np.sum(np.abs(got[sl] - ref) * np.diff(x)) / np.sum(np.abs(ref) * np.diff(x))
+        assert err <= TOL["float32"], (r, err)
+    assert plan.check_errors() == 0
