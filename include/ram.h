@@ -62,6 +62,9 @@ typedef enum { RAM_DONOR = 0, RAM_VANLEER = 1 } ram_scheme;
 #define RAM_LIMITER_OFF 1u  /* unlimited reconstruction (PLM centred slope, PPM
                                without App. A.2); makes the shift linear in Q */
 #define RAM_SHARED_MESH 2u  /* every row uses row 0's nodes (all rows equal N) */
+#define RAM_ADJOINT 4u      /* reserve the device scratch that ram_step_adjoint needs on
+                               rows with their own mesh when a residual step is
+                               present (2 x n_cells values of the plan's widest dtype) */
 
 /* largest residual sub-step count a row may ask for */
 #define RAM_MAX_NSUB 8
@@ -78,7 +81,7 @@ typedef struct {
                                   (2 = PLM, 3 = PPM, 4 = quartic cumulative); NULL ->
                                   default_order for every row */
     int8_t default_order;
-    uint32_t flags;            /* RAM_LIMITER_OFF | RAM_SHARED_MESH */
+    uint32_t flags;            /* RAM_LIMITER_OFF | RAM_SHARED_MESH | RAM_ADJOINT */
 } ram_mesh_desc;
 
 /* Build a plan for the rows in `desc` on CUDA device `device` (Sec. 2 mesh,

@@ -52,7 +52,8 @@ class RamSegment(torch.autograd.Function):
 def rollout(plan, q0, v0, dt: float, steps: int, dv=None, nsub=None,
             checkpoint_every: int = 20):
     """Advance q0 by `steps` RAM steps, differentiable with respect to q0 and dv.
-    The plan must be built with limiter=False (the transpose needs a linear step)."""
+    The plan must be built with limiter=False (the transpose needs a linear step),
+    and with adjoint=True when it has rows with their own mesh and dv is given."""
     q = q0
     done = 0
     while done < steps:

@@ -1,4 +1,5 @@
-// Transpose of one linear RAM step (limiter off, donor residual) on uniform rows.
+// Transpose of one linear RAM step (limiter off, donor residual) on uniform rows
+// (rows with their own mesh: ram_adjoint_nu.cu).
 //
 // With the limiters off the shift of a uniform row is a fixed stencil: output
 // cell m takes the right part of source cell p = m-K-1 and the left part of p+1
@@ -233,18 +234,21 @@ cudaError_t launch_adj_t(const Plan &p, const StepArgs &a, const void *g_out, vo
 cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
                            void *g_in, void *g_dv, cudaStream_t s)
 {
-    for (int o = 2; o <= 4; ++o)
-        if (!p.tiles_general_h[o].empty()) return cudaErrorNotSupported;
+    // rows with their own mesh and a residual step need the plan's scratch
+    const bool nonuni = p.n_uniform_rows < p.n_rows;
+    if (nonuni && a.dv != nullptr && p.adj_scratch == nullptr) return cudaErrorNotSupported;
     cudaError_t e = launch_params(p, dt, a, s);
     if (e != cudaSuccess) return e;
     if (dt == RAM_F32) {
         if ((e = launch_adj_t<float, 2>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
         if ((e = launch_adj_t<float, 3>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
-        return launch_adj_t<float, 4>(p, a, g_out, g_in, g_dv, s);
+        if ((e = launch_adj_t<float, 4>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
+    } else {
+        if ((e = launch_adj_t<double, 2>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
+        if ((e = launch_adj_t<double, 3>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
+        if ((e = launch_adj_t<double, 4>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
     }
-    if ((e = launch_adj_t<double, 2>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
-    if ((e = launch_adj_t<double, 3>(p, a, g_out, g_in, g_dv, s)) != cudaSuccess) return e;
-    return launch_adj_t<double, 4>(p, a, g_out, g_in, g_dv, s);
+    return nonuni ? launch_adjoint_nu(p, dt, a, g_out, g_in, g_dv, s) : cudaSuccess;
 }
 
 }  // namespace ram

@@ -143,6 +143,13 @@ struct Plan {
     int32_t gen32_whole[5] = {0};
     int32_t gen32_wcap[5][2] = {{0}};
     int32_t gen32_qcap[5][2] = {{0}};
+    // adjoint of rows with their own mesh: tiles of at most adj_nu_tcap cells per
+    // order, and (flag RAM_ADJOINT) scratch for the shifted field and the residual's
+    // cotangent, n_cells values each of the plan's widest dtype
+    std::vector<Tile> tiles_adj_nu_h[5];
+    Tile *tiles_adj_nu[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t adj_nu_tcap = 512;
+    void *adj_scratch = nullptr;
     std::vector<Tile> tiles_nseg_h;
     int32_t nseg_rows = 0;
     int32_t nu_kernel = 0;         // FP32 rows with their own mesh: 1 = warp-segment kernel
@@ -223,6 +230,9 @@ cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *
                             cudaStream_t s);
 cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
                            void *g_in, void *g_dv, cudaStream_t s);
+// rows with their own mesh (ram_adjoint_nu.cu)
+cudaError_t launch_adjoint_nu(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
+                              void *g_in, void *g_dv, cudaStream_t s);
 
 cudaError_t launch_rows(const Plan &p, ram_dtype dt, const StepArgs &a, cudaStream_t s,
                         int order, const RowPos *rows, int n_rows, int ncap);

@@ -73,6 +73,10 @@ void free_lists(Plan &p)
     cudaFree(p.tiles_nseg);
     p.tiles_nseg = nullptr;
     for (int o = 0; o < 5; ++o) {
+        cudaFree(p.tiles_adj_nu[o]);
+        p.tiles_adj_nu[o] = nullptr;
+    }
+    for (int o = 0; o < 5; ++o) {
         cudaFree(p.tiles_uniform[o]);
         cudaFree(p.tiles_general[o]);
         cudaFree(p.tiles_general32[o]);
@@ -103,6 +107,8 @@ void free_device(Plan &p)
     cudaFree(p.err);
     cudaFree(p.row_par);
     p.row_par = nullptr;
+    cudaFree(p.adj_scratch);
+    p.adj_scratch = nullptr;
     p.rows = nullptr;
     p.xfix = nullptr;
     p.dx32 = nullptr;
@@ -198,6 +204,7 @@ ram_status build_tiles(Plan &p)
     free_lists(p);
     p.tiles_nseg_h.clear();
     p.nseg_rows = 0;
+    for (int o = 0; o < 5; ++o) p.tiles_adj_nu_h[o].clear();
     for (int o = 0; o < 5; ++o) {
         p.tiles_uniform_h[o].clear();
         p.tiles_general_h[o].clear();
@@ -267,6 +274,9 @@ ram_status build_tiles(Plan &p)
         const double *x = (p.flags & RAM_SHARED_MESH) ? p.nodes_h.data()
                                                        : p.nodes_h.data() + p.row_offset[r] + r;
         const std::vector<double> w2 = doubled_widths(x, n);
+        // the adjoint's tiles: plain runs of at most adj_nu_tcap cells
+        for (int a = 0; a < n; a += p.adj_nu_tcap)
+            p.tiles_adj_nu_h[ri.order].push_back(Tile{r, a, std::min(p.adj_nu_tcap, n - a), 0});
         // FP32: the warp-segment kernel, with segments short enough that a segment
         // and its largest residual halo span less than a period, and a source
         // window that fits its shared-memory region
@@ -355,6 +365,10 @@ ram_status build_tiles(Plan &p)
                      });
     if (upload(&p.tiles_nseg, p.tiles_nseg_h.data(), p.tiles_nseg_h.size()) != cudaSuccess)
         return RAM_ERR_NOMEM;
+    for (int o = 2; o <= 4; ++o)
+        if (upload(&p.tiles_adj_nu[o], p.tiles_adj_nu_h[o].data(), p.tiles_adj_nu_h[o].size()) !=
+            cudaSuccess)
+            return RAM_ERR_NOMEM;
     // the rows' position units (qshift) live in the device row table
     if (p.rows && cudaMemcpy(p.rows, p.rows_h.data(), sizeof(RowInfo) * p.rows_h.size(),
                              cudaMemcpyHostToDevice) != cudaSuccess)
@@ -522,6 +536,8 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
             upload(&p->buckets, buckets.data(), buckets.size()) != cudaSuccess ||
             cudaMalloc((void **)&p->err, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->row_par, sizeof(RowParams<double>) * (size_t)nr) != cudaSuccess ||
+            ((desc->flags & RAM_ADJOINT) && p->n_uniform_rows < nr &&
+             cudaMalloc(&p->adj_scratch, 2 * sizeof(double) * (size_t)p->n_cells) != cudaSuccess) ||
             cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
             st = RAM_ERR_NOMEM;
     }

@@ -126,3 +126,124 @@ def test_rollout_gradients_finite_differences(n_r, n_phi, steps, k):
     g32q, g32dv = torch.autograd.grad(loss32, (q32, dv32))
     rel_q = float((g32q.double() - gq).abs().sum() / gq.abs().sum())
     assert rel_q <= 1e-3, rel_q
+
+
+def _nonuniform_batch(n_rows=7, seed=30, n_max=3000):
+    lens = np.random.default_rng(seed).integers(5, n_max, n_rows)
+    lens[0] = 3  # a row shorter than the stencil
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    nodes = np.concatenate([wl.random_nodes(int(n), seed=seed + r, ratio=4.0, x0=0.2 * r)
+                            for r, n in enumerate(lens)])
+    orders = np.array([(2, 3, 4)[r % 3] for r in range(n_rows)], dtype=np.int8)
+    return ro, nodes, orders
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("with_dv", [False, True])
+def test_adjoint_nonuniform_rows_match_oracle(dtype, with_dv):
+    """Rows with their own mesh (orders 2/3/4, one shorter than the stencil), per-row
+    shifts of many cells both ways, donor residual with 1-3 sub-steps: g_in and
+    dL/d dv against the oracle's transpose."""
+    ro, nodes, orders = _nonuniform_batch()
+    n_rows = ro.size - 1
+    plan = ram.Plan(ro, nodes, order=orders, limiter=False, adjoint=True)
+    assert plan.info().n_uniform_rows == 0
+    rng = np.random.default_rng(31)
+    n = int(ro[-1])
+    q = _t(1.0 + rng.random(n), dtype)
+    g = _t(rng.standard_normal(n), dtype)
+    dt = 0.5
+    v0 = rng.uniform(-40, 40, n_rows) / np.diff(ro) / dt
+    nsub = np.array([1 + r % 3 for r in range(n_rows)], dtype=np.int32)
+    dvh = None
+    if with_dv:
+        dvh = np.concatenate([
+            (rng.random(int(ro[r + 1] - ro[r])) - 0.5) * 1.6 * nsub[r] *
+            np.diff(nodes[ro[r] + r: ro[r + 1] + r + 1]).min() / dt for r in range(n_rows)])
+    dv = None if dvh is None else _t(dvh, dtype)
+    gin = torch.empty_like(q)
+    gdv = None if dv is None else torch.zeros_like(dv)
+    ram.step_adjoint(plan, q, g, gin, _t(v0, torch.float64), dt, dv=dv, g_dv=gdv,
+                     nsub=_t(nsub, torch.int32))
+    torch.cuda.synchronize()
+    tol = TOL["float64" if dtype == torch.float64 else "float32"]
+    gi = gin.double().cpu().numpy()
+    qr, gr = q.double().cpu().numpy(), g.double().cpu().numpy()
+    dvr = None if dv is None else dv.double().cpu().numpy()
+    gd = None if gdv is None else gdv.double().cpu().numpy()
+    for r in range(n_rows):
+        sl = slice(int(ro[r]), int(ro[r + 1]))
+        x = nodes[ro[r] + r: ro[r + 1] + r + 1]
+        ref_gi, ref_gd = oracle.step_adjoint(x, qr[sl], gr[sl],
+                                             oracle.shift_from_velocity(v0[r], dt), int(orders[r]),
+                                             None if dvr is None else dvr[sl], dt, int(nsub[r]))
+        e1 = np.abs(gi[sl] - ref_gi).sum() / np.abs(ref_gi).sum()
+        assert e1 <= tol, (r, int(orders[r]), e1)
+        if gd is not None:
+            e2 = np.abs(gd[sl] - ref_gd).sum() / np.abs(ref_gd).sum()
+            assert e2 <= tol, (r, e2)
+    assert plan.check_errors() == 0
+
+
+def test_adjoint_nonuniform_dot_product_and_scratch_flag():
+    """<J x, y> = <x, J^T y> on rows with their own mesh (FP64); without the
+    RAM_ADJOINT flag a step with a residual is refused (no scratch), one without
+    a residual is not."""
+    ro, nodes, orders = _nonuniform_batch(n_rows=5, seed=40)
+    n_rows = ro.size - 1
+    rng = np.random.default_rng(41)
+    n = int(ro[-1])
+    x = _t(rng.standard_normal(n), torch.float64)
+    y = _t(rng.standard_normal(n), torch.float64)
+    dt = 0.3
+    v0 = _t(rng.uniform(-9, 9, n_rows), torch.float64)
+    dv = _t(np.concatenate([(rng.random(int(ro[r + 1] - ro[r])) - 0.5) * 0.5 *
+                            np.diff(nodes[ro[r] + r: ro[r + 1] + r + 1]).min() / dt
+                            for r in range(n_rows)]), torch.float64)
+    plan = ram.Plan(ro, nodes, order=orders, limiter=False, adjoint=True)
+    jx, jty = torch.empty_like(x), torch.empty_like(y)
+    ram.step(plan, x, jx, v0, dt, dv=dv, scheme=ram.DONOR)
+    ram.step_adjoint(plan, x, y, jty, v0, dt, dv=dv)
+    torch.cuda.synchronize()
+    lhs, rhs = float((jx * y).sum()), float((x * jty).sum())
+    assert abs(lhs - rhs) <= 1e-13 * float((jx.abs() * y.abs()).sum())
+    bare = ram.Plan(ro, nodes, order=orders, limiter=False)
+    with pytest.raises(ram.RamError) as e:
+        ram.step_adjoint(bare, x, y, jty, v0, dt, dv=dv)
+    assert e.value.status == 7
+    ram.step_adjoint(bare, x, y, jty, v0, dt)
+    torch.cuda.synchronize()
+
+
+def test_rollout_gradients_nonuniform_finite_differences():
+    """Checkpointed rollout on rows with their own mesh (FP64): the autograd gradient
+    with respect to Q0 and dv against central differences on random directions."""
+    ro, nodes, orders = _nonuniform_batch(n_rows=4, seed=50, n_max=800)
+    n_rows = ro.size - 1
+    plan = ram.Plan(ro, nodes, order=orders, limiter=False, adjoint=True)
+    rng = np.random.default_rng(51)
+    n = int(ro[-1])
+    dt = 0.2
+    v0 = _t(rng.uniform(-20, 20, n_rows), torch.float64)
+    q0 = _t(1.0 + rng.random(n), torch.float64).requires_grad_(True)
+    dvh = np.concatenate([(0.3 + 0.4 * rng.random(int(ro[r + 1] - ro[r]))) *
+                          np.where(rng.random(int(ro[r + 1] - ro[r])) < 0.5, -1, 1) *
+                          np.diff(nodes[ro[r] + r: ro[r + 1] + r + 1]).min() / dt
+                          for r in range(n_rows)])
+    dv = _t(dvh, torch.float64).requires_grad_(True)
+    target = _t(1.0 + rng.random(n), torch.float64)
+    ns = _t(np.ones(n_rows), torch.int32)
+
+    def f(q, d):
+        return ((rollout(plan, q, v0, dt, 12, dv=d, nsub=ns, checkpoint_every=5) - target) ** 2).sum()
+
+    loss = f(q0, dv)
+    gq, gdv = torch.autograd.grad(loss, (q0, dv))
+    with torch.no_grad():
+        for d in range(6):
+            eq = _t(rng.standard_normal(n), torch.float64)
+            ev = _t(rng.standard_normal(n), torch.float64) * dv.abs().mean() * 1e-3
+            h = 1e-5
+            fd = (float(f(q0 + h * eq, dv + h * ev)) - float(f(q0 - h * eq, dv - h * ev))) / (2 * h)
+            an = float((gq * eq).sum() + (gdv * ev).sum())
+            assert fd == pytest.approx(an, rel=1e-6, abs=1e-9 * abs(float(loss))), d
