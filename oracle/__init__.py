@@ -59,6 +59,9 @@ def _load():
             ctypes.POINTER(ctypes.c_byte), i, d, d, ctypes.c_double, i,
             ctypes.POINTER(ctypes.c_int), d, d]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_a4_average.argtypes = [i, d, d]
+        lib.oracle_a4_point.argtypes = [i, d, d]
+        lib.oracle_step_a4.argtypes = [i, d, d, i, ctypes.c_double, d, ctypes.c_double, i, i, d]
         _lib = lib
     return _lib
 
@@ -219,6 +222,42 @@ def step_rows(row_offset, nodes, shared_mesh, order, limiter, shift_per_row, q_i
     return out
 
 
+def a4_average(q):
+    """Fourth-order cell averages from point values (Sec. 3.1), periodic."""
+    lib = _load()
+    q, qp = _f64(q)
+    out, op = _f64(np.empty(q.size))
+    _check(lib.oracle_a4_average(q.size, qp, op))
+    return out
+
+
+def a4_point(avg):
+    """Point values whose fourth-order cell averages are `avg` (periodic solve)."""
+    lib = _load()
+    a, ap = _f64(avg)
+    out, op = _f64(np.empty(a.size))
+    _check(lib.oracle_a4_point(a.size, ap, op))
+    return out
+
+
+def step_a4(x, q, s, limiter=True, dv=None, dt=0.0, scheme=VANLEER, nsub=1,
+            return_status=False):
+    """One RAM step with the A4 correction: PPM remap of the corrected averages,
+    point values recovered, then the residual step."""
+    lib = _load()
+    x, xp = _f64(x)
+    q, qp = _f64(q)
+    if dv is None:
+        dvp = None
+    else:
+        dv, dvp = _f64(dv)
+    out, op = _f64(np.empty(q.size))
+    st = lib.oracle_step_a4(q.size, xp, qp, int(bool(limiter)), float(s), dvp, float(dt),
+                            int(scheme), int(nsub), op)
+    _check(st, allow_cfl=True)
+    return (out, st) if return_status else out
+
+
 def num_threads():
     return _load().oracle_num_threads()
 
@@ -233,4 +272,5 @@ def mass(x, q):
 __all__ = ["shift", "reconstruct", "cell_cumulative", "residual", "step",
            "shift_adjoint", "residual_adjoint_donor", "step_adjoint",
            "shift_from_velocity", "phase_update", "step_rows", "num_threads", "mass",
+           "a4_average", "a4_point", "step_a4",
            "DONOR", "VANLEER", "OracleError"]

@@ -27,7 +27,17 @@
  *   - the PPM parabola variable is xi = (x - x_{i-1/2}) / dx_i in [0, 1] (Sec. 3.1).
  *   - order 4 is not in the paper: the in-cell cumulative is the mean of the two
  *     quartic interpolants of the cumulative mass through the node sets
- *     {i-5/2..i+3/2} and {i-3/2..i+5/2}; unlimited.
+ *     {i-5/2..i+3/2} and {i-3/2..i+5/2}.  With the limiter on it is scaled toward
+ *     the cell mean (the maximum-principle scaling limiter of Zhang & Shu 2010):
+ *     q~ = Q_i + theta (q - Q_i), theta the largest value in [0, 1] that keeps q~
+ *     inside [min, max] of Q_{i-1}, Q_i, Q_{i+1} on the whole cell; the mean, and so
+ *     the mass, is unchanged.
+ *   - the fourth-order cell-average correction of Sec. 3.1 (A4): the stored values
+ *     are point values Q_i; the remap works on <Q>_i = Q_i + (Q_{i+1} - 2Q_i +
+ *     Q_{i-1}) / 24 (PPM) and the new point values solve the same relation for the
+ *     remapped averages (a periodic tridiagonal system), so sum_i Q_i dx_i is
+ *     conserved on a periodic uniform mesh; the residual step then acts on the point
+ *     values.
  *   - limiter off: PLM takes the centred slope, PPM skips both limiter stages.
  *   - the residual step (only named in the paper, Sec. 4 and Eq. 6) is a flux-form
  *     upwind step at the interfaces: donor cell, or van Leer (PLM, van Leer slope,
@@ -173,8 +183,11 @@ typedef struct {
     const double *q;
     double *dx;
     double *m;      /* masses M_i = Q_i dx_i (Eq. 3) */
-    double *c0, *c1, *c2; /* PLM: (Q, sigma, -); PPM: (QL, QR, Q6); order 4: unused */
+    double *c0, *c1, *c2; /* PLM: (Q, sigma, -); PPM: (QL, QR, Q6); order 4: (theta, -, -) */
+    int limited;          /* order 4 with the scaling limiter */
 } recon_t;
+
+static double quartic_theta(const recon_t *r, int i);
 
 static int recon_build(recon_t *r, int n, const double *x, const double *q,
                        int order, int limiter)
@@ -191,12 +204,19 @@ static int recon_build(recon_t *r, int n, const double *x, const double *q,
     int st = widths(n, x, r->dx);
     if (st) return st;
     for (int i = 0; i < n; ++i) r->m[i] = q[i] * r->dx[i];
+    r->limited = 0;
     if (order == 2) {
         for (int i = 0; i < n; ++i) r->c0[i] = q[i];
         plm_slopes(n, r->dx, q, limiter, r->c1);
     } else if (order == 3) {
         ppm_coefs(n, r->dx, q, limiter, r->c0, r->c1, r->c2);
-    } else if (order != 4) {
+    } else if (order == 4) {
+        for (int i = 0; i < n; ++i) r->c0[i] = 1.0;
+        if (limiter) {
+            for (int i = 0; i < n; ++i) r->c0[i] = quartic_theta(r, i);
+            r->limited = 1;
+        }
+    } else {
         return ORC_ERR_ARG;
     }
     return ORC_OK;
@@ -277,8 +297,98 @@ static double cell_G(const recon_t *r, int i, double d)
         quartic_values(r, i, v);
         quartic_pair_weights(z, d, w);
         for (int k = 0; k < 6; ++k) g += w[k] * v[k];
+        if (r->limited) {
+            /* the profile scaled toward the mean: G~ = theta G + (1 - theta) Q d */
+            double th = r->c0[i];
+            g = th * g + (1.0 - th) * r->q[i] * d;
+        }
         return g;
     }
+}
+
+/* Order-4 scaling limiter: theta in [0, 1] such that Q_i + theta (q_i(x) - Q_i)
+ * stays within [min, max] of Q_{i-1}, Q_i, Q_{i+1} over the cell.  q_i = dG_i/dx is
+ * a cubic; its power-basis coefficients come from G_i at xi = 1/4, 1/2, 3/4, 1 (a
+ * 4 x 4 Vandermonde system, Gaussian elimination), and its extremes are at the
+ * cell's ends or at the real roots of q' inside the cell. */
+static double quartic_theta(const recon_t *r, int i)
+{
+    int n = r->n;
+    double h = r->dx[i], Q = r->q[i];
+    double qm = r->q[cyc(i - 1, n)], qp = r->q[cyc(i + 1, n)];
+    double lo = Q, hi = Q;
+    if (qm < lo) lo = qm;
+    if (qp < lo) lo = qp;
+    if (qm > hi) hi = qm;
+    if (qp > hi) hi = qp;
+    /* G(xi h) / h = a1 xi + a2 xi^2 + a3 xi^3 + a4 xi^4 */
+    double A[4][5];
+    recon_t u = *r;
+    u.limited = 0;
+    for (int k = 0; k < 4; ++k) {
+        double xi = 0.25 * (k + 1), p = xi;
+        for (int j = 0; j < 4; ++j) {
+            A[k][j] = p;
+            p *= xi;
+        }
+        A[k][4] = cell_G(&u, i, xi * h) / h;
+    }
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+        for (int k = c + 1; k < 4; ++k)
+            if (fabs(A[k][c]) > fabs(A[piv][c])) piv = k;
+        for (int j = 0; j < 5; ++j) {
+            double t = A[c][j];
+            A[c][j] = A[piv][j];
+            A[piv][j] = t;
+        }
+        for (int k = c + 1; k < 4; ++k) {
+            double f = A[k][c] / A[c][c];
+            for (int j = c; j < 5; ++j) A[k][j] -= f * A[c][j];
+        }
+    }
+    double a[4];
+    for (int c = 3; c >= 0; --c) {
+        double t = A[c][4];
+        for (int j = c + 1; j < 4; ++j) t -= A[c][j] * a[j];
+        a[c] = t / A[c][c];
+    }
+    /* q(xi) = a1 + 2 a2 xi + 3 a3 xi^2 + 4 a4 xi^3; q'(xi) = 2 a2 + 6 a3 xi + 12 a4 xi^2 */
+    double cand[4];
+    int nc = 0;
+    cand[nc++] = 0.0;
+    cand[nc++] = 1.0;
+    double qa = 12.0 * a[3], qb = 6.0 * a[2], qc = 2.0 * a[1];
+    if (fabs(qa) > 1e-300) {
+        double disc = qb * qb - 4.0 * qa * qc;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            double r1 = (-qb - sq) / (2.0 * qa), r2 = (-qb + sq) / (2.0 * qa);
+            if (r1 > 0.0 && r1 < 1.0) cand[nc++] = r1;
+            if (r2 > 0.0 && r2 < 1.0) cand[nc++] = r2;
+        }
+    } else if (fabs(qb) > 1e-300) {
+        double r1 = -qc / qb;
+        if (r1 > 0.0 && r1 < 1.0) cand[nc++] = r1;
+    }
+    double qmax = -INFINITY, qmin = INFINITY;
+    for (int k = 0; k < nc; ++k) {
+        double xi = cand[k];
+        double v = a[0] + xi * (2.0 * a[1] + xi * (3.0 * a[2] + xi * 4.0 * a[3]));
+        if (v > qmax) qmax = v;
+        if (v < qmin) qmin = v;
+    }
+    double th = 1.0;
+    if (qmax > hi && qmax - Q > 0.0) {
+        double t = (hi - Q) / (qmax - Q);
+        if (t < th) th = t;
+    }
+    if (qmin < lo && qmin - Q < 0.0) {
+        double t = (lo - Q) / (qmin - Q);
+        if (t < th) th = t;
+    }
+    if (th < 0.0) th = 0.0;
+    return th;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -595,6 +705,93 @@ int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fourth-order cell-average correction (Sec. 3.1)                              */
+/* ------------------------------------------------------------------------- */
+
+/* <Q>_i = Q_i + (Q_{i+1} - 2 Q_i + Q_{i-1}) / 24, periodic. */
+int oracle_a4_average(int n, const double *q, double *avg)
+{
+    if (n < 1) return ORC_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        avg[i] = q[i] + (q[cyc(i + 1, n)] - 2.0 * q[i] + q[cyc(i - 1, n)]) / 24.0;
+    return ORC_OK;
+}
+
+/* The point values whose corrected averages are `avg`: the periodic tridiagonal
+ * system Q_{i-1} + 22 Q_i + Q_{i+1} = 24 <Q>_i, solved by the Thomas algorithm
+ * with the Sherman-Morrison correction for the two corner entries. */
+int oracle_a4_point(int n, const double *avg, double *q)
+{
+    if (n < 1) return ORC_ERR_ARG;
+    if (n == 1) {
+        q[0] = avg[0];
+        return ORC_OK;
+    }
+    if (n == 2) {
+        /* 22 q0 + 2 q1 = 24 a0, 2 q0 + 22 q1 = 24 a1 */
+        double det = 22.0 * 22.0 - 4.0;
+        q[0] = (22.0 * 24.0 * avg[0] - 2.0 * 24.0 * avg[1]) / det;
+        q[1] = (22.0 * 24.0 * avg[1] - 2.0 * 24.0 * avg[0]) / det;
+        return ORC_OK;
+    }
+    double *b = (double *)malloc(sizeof(double) * (size_t)n);
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    double *z = (double *)malloc(sizeof(double) * (size_t)n);
+    double *u = (double *)calloc((size_t)n, sizeof(double));
+    double *cp = (double *)malloc(sizeof(double) * (size_t)n);
+    double gamma = -22.0, alpha = 1.0, beta = 1.0; /* corners A[n-1][0], A[0][n-1] */
+    for (int i = 0; i < n; ++i) b[i] = 22.0;
+    b[0] -= gamma;
+    b[n - 1] -= alpha * beta / gamma;
+    u[0] = gamma;
+    u[n - 1] = alpha;
+    /* solve T y = 24 avg and T z = u (T tridiagonal with unit off-diagonals) */
+    for (int pass = 0; pass < 2; ++pass) {
+        double *out = pass == 0 ? y : z;
+        for (int i = 0; i < n; ++i) out[i] = pass == 0 ? 24.0 * avg[i] : u[i];
+        cp[0] = 1.0 / b[0];
+        out[0] = out[0] / b[0];
+        for (int i = 1; i < n; ++i) {
+            double m = b[i] - cp[i - 1];
+            cp[i] = 1.0 / m;
+            out[i] = (out[i] - out[i - 1]) / m;
+        }
+        for (int i = n - 2; i >= 0; --i) out[i] -= cp[i] * out[i + 1];
+    }
+    double f = (y[0] + beta * y[n - 1] / gamma) / (1.0 + z[0] + beta * z[n - 1] / gamma);
+    for (int i = 0; i < n; ++i) q[i] = y[i] - f * z[i];
+    free(b);
+    free(y);
+    free(z);
+    free(u);
+    free(cp);
+    return ORC_OK;
+}
+
+/* One RAM step with the A4 correction: PPM remap of the corrected averages, the
+ * point values recovered from the remapped averages, then the residual step. */
+int oracle_step_a4(int n, const double *x, const double *q_in, int limiter, double s,
+                   const double *dv, double dt, int scheme, int nsub, double *q_out)
+{
+    double *avg = (double *)malloc(sizeof(double) * (size_t)n);
+    double *sh = (double *)malloc(sizeof(double) * (size_t)n);
+    double *pt = (double *)malloc(sizeof(double) * (size_t)n);
+    int st = oracle_a4_average(n, q_in, avg);
+    if (!st) st = oracle_shift(n, x, avg, 3, limiter, s, sh);
+    if (!st) st = oracle_a4_point(n, sh, pt);
+    if (!st) {
+        if (dv)
+            st = oracle_residual(n, x, pt, dv, dt, scheme, nsub, q_out);
+        else
+            memcpy(q_out, pt, sizeof(double) * (size_t)n);
+    }
+    free(avg);
+    free(sh);
+    free(pt);
+    return st;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -48,6 +48,15 @@ MUTANTS = {
     "rows_nsub_index": ("nsub ? nsub[r] : 1", "nsub ? nsub[0] : 1"),
     "rows_dv_offset": ("dv ? dv + b : NULL", "dv ? dv : NULL"),
     "rows_shared_mesh_ignored": ("shared_mesh ? nodes : nodes + b + r;", "nodes + b + r;"),
+    "a4_factor": ("2.0 * q[i] + q[cyc(i - 1, n)]) / 24.0;", "2.0 * q[i] + q[cyc(i - 1, n)]) / 12.0;"),
+    "a4_inverse_diagonal": ("for (int i = 0; i < n; ++i) b[i] = 22.0;",
+                            "for (int i = 0; i < n; ++i) b[i] = 20.0;"),
+    "a4_sherman_morrison_sign": ("double f = (y[0] + beta * y[n - 1] / gamma)",
+                                 "double f = (y[0] - beta * y[n - 1] / gamma)"),
+    "limited4_bound_neighbour": ("if (qp > hi) hi = qp;", "if (qp > hi) hi = Q;"),
+    "limited4_blend": ("g = th * g + (1.0 - th) * r->q[i] * d;",
+                       "g = th * g + (1.0 - th) * r->q[i] * r->dx[i];"),
+    "limited4_theta": ("double t = (hi - Q) / (qmax - Q);", "double t = (hi - Q) / (qmax + Q);"),
 }
 
 

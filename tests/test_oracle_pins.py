@@ -611,3 +611,135 @@ def test_step_rows_whole_cell_rolls():
     for r, (n, k) in enumerate(zip(lens, ks)):
         sl = slice(int(ro[r]), int(ro[r + 1]))
         assert np.array_equal(got[sl], np.roll(q[sl], k)), r
+
+
+# ---------------------------------------------------------------------------
+# the fourth-order cell-average correction (Sec. 3.1) and the limited order 4
+# ---------------------------------------------------------------------------
+
+def test_a4_averages_are_exact_for_cubics():
+    """Point values of a cubic at the cell centres of a uniform mesh: the A4 formula
+    gives the exact cell averages (away from the periodic seam, where the cubic
+    itself is not periodic)."""
+    n = 40
+    x = wl.uniform_nodes(n, -1.0, 2.0)
+    c = np.array([0.3, -1.2, 0.7, 2.1])  # c0 + c1 t + c2 t^2 + c3 t^3
+    xc = 0.5 * (x[1:] + x[:-1])
+    pts = np.polyval(c[::-1], xc)
+    prim = np.polyint(c[::-1])
+    exact = (np.polyval(prim, x[1:]) - np.polyval(prim, x[:-1])) / np.diff(x)
+    avg = oracle.a4_average(pts)
+    np.testing.assert_allclose(avg[1:-1], exact[1:-1], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 64])
+def test_a4_inverse_round_trip_and_sum(n):
+    """The point values recovered from the corrected averages are the original ones,
+    and the correction keeps the sum (Eq. 10 on a periodic uniform mesh)."""
+    q = 1.0 + np.random.default_rng(n).random(n)
+    avg = oracle.a4_average(q)
+    np.testing.assert_allclose(oracle.a4_point(avg), q, rtol=0, atol=1e-14)
+    assert abs(avg.sum() - q.sum()) <= 1e-14 * q.sum()
+    # the inverse is an independent solve: check A4(a4_point(b)) == b for any b
+    b = np.random.default_rng(n + 1).standard_normal(n)
+    np.testing.assert_allclose(oracle.a4_average(oracle.a4_point(b)), b, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("limiter", [True, False])
+def test_a4_step_conservation_roll_and_identity(limiter):
+    n = 96
+    x = wl.uniform_nodes(n)
+    q = wl.three_gaussians(x, 7)
+    m0 = q.sum()
+    for s in (0.0, 0.37, -2.71, 5.0 / n, 123.456):
+        out = oracle.step_a4(x, q, s, limiter)
+        assert abs(out.sum() - m0) <= 1e-13 * m0, s
+    np.testing.assert_allclose(oracle.step_a4(x, q, 0.0, limiter), q, rtol=0, atol=1e-14)
+    # a whole-cell shift commutes with the circulant correction: a cyclic roll
+    np.testing.assert_allclose(oracle.step_a4(x, q, 7.0 / n, limiter), np.roll(q, 7),
+                               rtol=0, atol=1e-13)
+
+
+def test_a4_interface_values_fourth_order():
+    """Sec. 3.1: identifying <Q>_i with the point value Q_i is second order, which
+    limits the PPM interface values; with the corrected averages they converge at
+    fourth order (smooth periodic function sampled at the cell centres; unlimited
+    PPM faces against the exact values at the nodes)."""
+    def f(t):
+        return np.sin(2 * np.pi * t) + 0.4 * np.cos(6 * np.pi * t + 0.3)
+
+    ns = [32, 64, 128, 256]
+    errs = {False: [], True: []}
+    for n in ns:
+        x = wl.uniform_nodes(n)
+        pts = f(0.5 * (x[1:] + x[:-1]))
+        for a4 in (False, True):
+            avg = oracle.a4_average(pts) if a4 else pts
+            qr = oracle.reconstruct(x, avg, order=3, limiter=False)[:, 1]  # QR_i = face i+1/2
+            errs[a4].append(np.max(np.abs(qr - f(x[1:]))))
+    slope = {k: -np.polyfit(np.log(ns), np.log(v), 1)[0] for k, v in errs.items()}
+    assert abs(slope[False] - 2.0) < 0.2, slope
+    assert slope[True] > 3.8, slope
+
+
+def test_limited_order4_keeps_linear_profiles():
+    """A linear profile is reproduced by the quartic and already inside the
+    neighbours' range: the limiter leaves it alone."""
+    n = 60
+    x = wl.random_nodes(n, seed=70, ratio=1.5)
+    xc = 0.5 * (x[1:] + x[:-1])
+    q = 2.0 + 0.5 * xc
+    cells = np.arange(5, 55)
+    d = 0.37 * np.diff(x)[cells]
+    a = oracle.cell_cumulative(x, q, cells, d, order=4, limiter=True)
+    b = oracle.cell_cumulative(x, q, cells, d, order=4, limiter=False)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_limited_order4_profile_inside_neighbour_range(seed):
+    """Brute force: the limited profile dG/dx, sampled densely in every cell, stays
+    within [min, max] of the cell and its two neighbours, and integrates to the
+    cell's mass."""
+    n = 30
+    x = wl.random_nodes(n, seed=80 + seed, ratio=3.0)
+    q = np.random.default_rng(seed).random(n)
+    q[10:15] = 3.0  # a plateau: the unlimited quartic overshoots next to it
+    dx = np.diff(x)
+    m = 400
+    for i in range(n):
+        d = np.linspace(0.0, dx[i], m + 1)
+        G = oracle.cell_cumulative(x, q, np.full(m + 1, i), d, order=4, limiter=True)
+        # the profile dG/dx at the sample points, by differences of step eps
+        eps = 1e-7 * dx[i]
+        dl = np.clip(d - eps, 0.0, dx[i])
+        dr = np.clip(d + eps, 0.0, dx[i])
+        Gl = oracle.cell_cumulative(x, q, np.full(m + 1, i), dl, order=4, limiter=True)
+        Gr = oracle.cell_cumulative(x, q, np.full(m + 1, i), dr, order=4, limiter=True)
+        prof = (Gr - Gl) / (dr - dl)
+        lo = min(q[i - 1], q[i], q[(i + 1) % n])
+        hi = max(q[i - 1], q[i], q[(i + 1) % n])
+        assert prof.min() >= lo - 1e-7 and prof.max() <= hi + 1e-7, i
+        assert abs(G[-1] - q[i] * dx[i]) <= 1e-13 * abs(q[i] * dx[i])
+        # where the limiter acts, theta is the largest admissible value: the
+        # scaled profile reaches one of the bounds
+        Gu = oracle.cell_cumulative(x, q, np.full(m + 1, i), d, order=4, limiter=False)
+        if np.max(np.abs(G - Gu)) > 1e-12 * abs(q[i] * dx[i]):
+            gap = min(hi - prof.max(), prof.min() - lo)
+            assert gap <= 1e-5 * (hi - lo), (i, gap)
+
+
+def test_limited_order4_no_new_extrema_and_conservation():
+    """The limited order 4 creates no new extrema on a square wave over many shifts
+    (the unlimited one overshoots) and conserves the mass (Eq. 10)."""
+    n = 128
+    x = wl.random_nodes(n, seed=90, ratio=2.0)
+    xc = 0.5 * (x[1:] + x[:-1])
+    q0 = np.where((xc > 0.3) & (xc < 0.6), 1.0, 0.0)
+    ql, qu = q0.copy(), q0.copy()
+    for _ in range(20):
+        ql = oracle.shift(x, ql, 0.0173, 4, True)
+        qu = oracle.shift(x, qu, 0.0173, 4, False)
+    assert ql.max() <= 1.0 + 1e-12 and ql.min() >= -1e-12
+    assert qu.max() > 1.0 + 1e-3 or qu.min() < -1e-3
+    assert abs(oracle.mass(x, ql) - oracle.mass(x, q0)) <= 1e-13 * oracle.mass(x, q0)
