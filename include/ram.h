@@ -65,6 +65,14 @@ typedef enum { RAM_DONOR = 0, RAM_VANLEER = 1 } ram_scheme;
 #define RAM_ADJOINT 4u      /* reserve the device scratch that ram_step_adjoint needs on
                                rows with their own mesh when a residual step is
                                present (2 x n_cells values of the plan's widest dtype) */
+#define RAM_A4 8u           /* the fourth-order cell-average correction of Sec. 3.1: the
+                               cell arrays hold point values; ram_shift and ram_step remap
+                               <Q>_i = Q_i + (Q_{i+1} - 2Q_i + Q_{i-1}) / 24 with PPM and
+                               return the point values whose corrected averages are the
+                               remapped ones (the periodic tridiagonal inverse), then the
+                               residual step acts on the point values.  Every row must be
+                               uniform and of order 3 (else RAM_ERR_UNSUPPORTED); reserves
+                               2 x n_cells values of scratch; no adjoint. */
 
 /* largest residual sub-step count a row may ask for */
 #define RAM_MAX_NSUB 8
@@ -78,10 +86,12 @@ typedef struct {
                                   nodes[row_offset[r] + r .. row_offset[r+1] + r].
                                   RAM_SHARED_MESH: nodes[0 .. N] only. */
     const int8_t *order;       /* host, per-row reconstruction order p in {2,3,4}
-                                  (2 = PLM, 3 = PPM, 4 = quartic cumulative); NULL ->
+                                  (2 = PLM, 3 = PPM, 4 = quartic cumulative, with the
+                                  limiter on scaled toward the cell mean within the
+                                  range of the cell and its neighbours); NULL ->
                                   default_order for every row */
     int8_t default_order;
-    uint32_t flags;            /* RAM_LIMITER_OFF | RAM_SHARED_MESH | RAM_ADJOINT */
+    uint32_t flags;            /* RAM_LIMITER_OFF | RAM_SHARED_MESH | RAM_ADJOINT | RAM_A4 */
 } ram_mesh_desc;
 
 /* Build a plan for the rows in `desc` on CUDA device `device` (Sec. 2 mesh,
@@ -243,7 +253,8 @@ ram_status ram_plan_autotune(ram_plan plan, ram_dtype dtype, const void *q_in, v
  * counterpart: it is a plan-free variant of ram_step for n_rows rows of
  * n_cells_per_row cells each, packed back to back, all on one uniform periodic
  * mesh of period `period` (the rings of a disk), with reconstruction `order`
- * (2, 3, 4) and flags 0 or RAM_LIMITER_OFF.  The other arguments are those of
+ * (2, 3, 4; order 4 only with RAM_LIMITER_OFF, else RAM_ERR_UNSUPPORTED) and
+ * flags 0 or RAM_LIMITER_OFF.  The other arguments are those of
  * ram_step (no phase).  Its row table, row list and per-row shift parameters
  * live in one static device array of about 0.6 MiB that every GPU loading the
  * library keeps until the process exits; rows beyond RAM_STATIC_MAX_ROWS are

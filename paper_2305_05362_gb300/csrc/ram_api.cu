@@ -97,6 +97,33 @@ ram_status run(const Plan *p, ram_dtype dt, const StepArgs &a0, void *stream)
     return e == cudaSuccess ? RAM_OK : RAM_ERR_CUDA;
 }
 
+// A step of an A4 plan: corrected averages of the input, the shift of them,
+// point values back, then the residual step (if any) on the point values.
+ram_status run_a4(const Plan *p, ram_dtype dt, const StepArgs &a0, void *stream)
+{
+    DeviceGuard g(p->device);
+    if (!g.ok) return RAM_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *s1 = static_cast<char *>(p->a4_scratch);
+    char *s2 = s1 + (size_t)p->n_cells * sizeof(double);
+    const bool resid = a0.mode == MODE_STEP && a0.dv != nullptr;
+    if (launch_a4(*p, dt, a0.q_in, s1, s, true) != cudaSuccess) return RAM_ERR_CUDA;
+    StepArgs a1 = a0;
+    a1.q_in = s1;
+    a1.q_out = s2;
+    a1.dv = nullptr;
+    ram_status st = run(p, dt, a1, stream);
+    if (st != RAM_OK) return st;
+    if (launch_a4(*p, dt, s2, resid ? static_cast<void *>(s1) : a0.q_out, s, false) != cudaSuccess)
+        return RAM_ERR_CUDA;
+    if (!resid) return RAM_OK;
+    StepArgs a2 = a0;
+    a2.mode = MODE_RESIDUAL;
+    a2.q_in = s1;
+    a2.phase = nullptr;
+    return run(p, dt, a2, stream);
+}
+
 }  // namespace
 
 extern "C" ram_status ram_shift(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
@@ -109,7 +136,7 @@ extern "C" ram_status ram_shift(ram_plan plan, ram_dtype dtype, const void *q_in
     StepArgs a = base_args(p, q_in, q_out);
     a.mode = MODE_SHIFT;
     a.shift = shift;
-    return run(p, dtype, a, stream);
+    return p->a4 ? run_a4(p, dtype, a, stream) : run(p, dtype, a, stream);
 }
 
 extern "C" ram_status ram_residual_upwind(ram_plan plan, ram_dtype dtype, const void *q_in,
@@ -150,7 +177,7 @@ extern "C" ram_status ram_step(ram_plan plan, ram_dtype dtype, const void *q_in,
     a.dv = dv_iface;
     a.nsub = nsub;
     a.scheme = scheme;
-    return run(p, dtype, a, stream);
+    return p->a4 ? run_a4(p, dtype, a, stream) : run(p, dtype, a, stream);
 }
 
 extern "C" ram_status ram_step_adjoint(ram_plan plan, ram_dtype dtype, const void *q_in,
@@ -162,7 +189,7 @@ extern "C" ram_status ram_step_adjoint(ram_plan plan, ram_dtype dtype, const voi
     ram_status st = check_common(p, dtype, g_out, g_in);
     if (st != RAM_OK) return st;
     if (!q_in || !v0) return RAM_ERR_ARG;
-    if (p->limiter) return RAM_ERR_UNSUPPORTED;  // the transpose needs a linear step
+    if (p->limiter || p->a4) return RAM_ERR_UNSUPPORTED;  // the transpose: linear step, no A4
     if (!(dt >= 0.0) || dt > 1e300) return RAM_ERR_ARG;
     const size_t bytes = (size_t)p->n_cells * dtype_size(dtype);
     if (overlaps(q_in, g_in, bytes)) return RAM_ERR_ARG;

@@ -395,6 +395,49 @@ __device__ __forceinline__ void advance_phase(const StepArgs &a, const RowInfo &
     a.phase[r] = reduce_mod_rcp(a.phase[r] + sft, row.period, row.inv_period);
 }
 
+// Limited order 4: the scaling toward the cell mean of the maximum-principle
+// limiter of Zhang & Shu (2010).  a1..a4 are the power-basis coefficients of the
+// in-cell cumulative G(xi h) / h = a1 xi + a2 xi^2 + a3 xi^3 + a4 xi^4, so the
+// profile is q(xi) = a1 + 2 a2 xi + 3 a3 xi^2 + 4 a4 xi^3; its extremes over the
+// cell are at the ends or at the real roots of q' inside it.  Returns the largest
+// theta in [0, 1] with Q + theta (q - Q) inside [lo, hi] on the whole cell.
+template <typename T>
+__device__ __forceinline__ T quartic_scaling_theta(T a1, T a2, T a3, T a4, T Q, T lo, T hi)
+{
+    T qmax = a1, qmin = a1;  // xi = 0
+    const T q1 = a1 + T(2) * a2 + T(3) * a3 + T(4) * a4;  // xi = 1
+    qmax = fmax(qmax, q1);
+    qmin = fmin(qmin, q1);
+    // q'(xi) = 2 a2 + 6 a3 xi + 12 a4 xi^2
+    const T A = T(12) * a4, B = T(6) * a3, C = T(2) * a2;
+    T r[2];
+    int nr = 0;
+    if (fabs(A) > T(1e-30)) {
+        const T disc = B * B - T(4) * A * C;
+        if (disc >= T(0)) {
+            const T sq = sqrt(disc);
+            r[0] = (-B - sq) / (T(2) * A);
+            r[1] = (-B + sq) / (T(2) * A);
+            nr = 2;
+        }
+    } else if (fabs(B) > T(1e-30)) {
+        r[0] = -C / B;
+        nr = 1;
+    }
+    for (int k = 0; k < nr; ++k) {
+        const T x = r[k];
+        if (x > T(0) && x < T(1)) {
+            const T v = a1 + x * (T(2) * a2 + x * (T(3) * a3 + x * T(4) * a4));
+            qmax = fmax(qmax, v);
+            qmin = fmin(qmin, v);
+        }
+    }
+    T th = T(1);
+    if (qmax > hi && qmax - Q > T(0)) th = fmin(th, (hi - Q) / (qmax - Q));
+    if (qmin < lo && qmin - Q < T(0)) th = fmin(th, (lo - Q) / (qmin - Q));
+    return fmax(th, T(0));
+}
+
 // Wait until the kernels this one depends on (programmatic dependent launch)
 // have finished and their writes are visible; a no-op for a normal launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

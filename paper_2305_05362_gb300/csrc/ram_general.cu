@@ -245,7 +245,14 @@ __device__ T cell_G(const T *q, const T *dx, int p, T xi, bool lim)
         const T dR = Num<T>::div(f3145 - d3, z5);
         const T D = T(0.5) * (dL + dR);
         const T g = xi * (d1 + (xi - T(1)) * (d2 + (xi - z1) * (d3 + D * (xi - z4))));
-        return h * g;
+        if (!lim) return h * g;
+        // limited order 4: the profile scaled toward the mean (Zhang-Shu), bounded by
+        // the cell and its neighbours; the power-basis coefficients of G/h first
+        const T A0 = d3 - D * z4, B0 = -z1 * A0, B1 = A0 - z1 * D, C0 = d2 + B0;
+        const T th = quartic_scaling_theta<T>(d1 - C0, C0 - B1, B1 - D, D, q[p],
+                                              fmin(q[p], fmin(q[p - 1], q[p + 1])),
+                                              fmax(q[p], fmax(q[p - 1], q[p + 1])));
+        return h * (th * g + (T(1) - th) * q[p] * xi);
     }
 }
 

@@ -150,6 +150,10 @@ struct Plan {
     Tile *tiles_adj_nu[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t adj_nu_tcap = 512;
     void *adj_scratch = nullptr;
+    // the fourth-order cell-average correction (flag RAM_A4): scratch for the
+    // corrected averages and the remapped ones, n_cells values each (FP64 size)
+    int32_t a4 = 0;
+    void *a4_scratch = nullptr;
     std::vector<Tile> tiles_nseg_h;
     int32_t nseg_rows = 0;
     int32_t nu_kernel = 0;         // FP32 rows with their own mesh: 1 = warp-segment kernel
@@ -230,6 +234,10 @@ cudaError_t launch_row_mass(const Plan &p, ram_dtype dt, const void *q, double *
                             cudaStream_t s);
 cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
                            void *g_in, void *g_dv, cudaStream_t s);
+// the fourth-order cell-average correction (ram_a4.cu): to_avg: point values to
+// corrected averages, else the inverse
+cudaError_t launch_a4(const Plan &p, ram_dtype dt, const void *in, void *out, cudaStream_t s,
+                      bool to_avg);
 // rows with their own mesh (ram_adjoint_nu.cu)
 cudaError_t launch_adjoint_nu(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
                               void *g_in, void *g_dv, cudaStream_t s);

@@ -94,6 +94,8 @@ extern "C" ram_status ram_step_uniform_noalloc(ram_dtype dtype, int32_t n_rows,
     if (!(period > 0.0) || period > 1e300) return RAM_ERR_MESH;
     if (order < 2 || order > 4) return RAM_ERR_ARG;
     if (flags & ~RAM_LIMITER_OFF) return RAM_ERR_ARG;
+    // the limited order 4 needs per-cell work the uniform-row kernels do not do
+    if (order == 4 && !(flags & RAM_LIMITER_OFF)) return RAM_ERR_UNSUPPORTED;
     if (scheme != RAM_DONOR && scheme != RAM_VANLEER) return RAM_ERR_ARG;
     if (!(dt >= 0.0) || dt > 1e300) return RAM_ERR_ARG;
     if (!q_in || !q_out || !v0) return RAM_ERR_ARG;

@@ -166,6 +166,7 @@ __device__ __forceinline__ void recon_ppm(float L, float R, float Q, float h, fl
 // cumulative mass through the nodes {k-5/2..k+3/2} and {k-3/2..k+5/2}, in Newton
 // form about x_{k-1/2} (z: node offsets in units of h0, v: cumulative mass / h0),
 // expanded to the power basis.  q[0..4], h[0..4]: cells k-2 .. k+2.
+template <bool LIM>
 __device__ __forceinline__ void recon_quartic(const float *q, const float *h, float b[4])
 {
     const float ih = rcp_approx(h[2]);
@@ -193,10 +194,22 @@ __device__ __forceinline__ void recon_quartic(const float *q, const float *h, fl
     const float B0 = -z1 * A0, B1 = A0 - z1 * D;  // (xi - z1)(A0 + D xi)
     const float C0 = d2 + B0;                     // d2 + ... = C0 + B1 xi + D xi^2
     const float hh = h[2];
-    b[0] = hh * (d1 - C0);
-    b[1] = hh * (C0 - B1);
-    b[2] = hh * (B1 - D);
-    b[3] = hh * D;
+    float a1 = d1 - C0, a2 = C0 - B1, a3 = B1 - D, a4 = D;
+    if (LIM) {
+        // limited order 4: scaled toward the mean (Zhang-Shu), bounded by the cell
+        // and its neighbours
+        const float th = quartic_scaling_theta<float>(a1, a2, a3, a4, q[2],
+                                                      fminf(q[2], fminf(q[1], q[3])),
+                                                      fmaxf(q[2], fmaxf(q[1], q[3])));
+        a1 = th * a1 + (1.f - th) * q[2];
+        a2 *= th;
+        a3 *= th;
+        a4 *= th;
+    }
+    b[0] = hh * a1;
+    b[1] = hh * a2;
+    b[2] = hh * a3;
+    b[3] = hh * a4;
 }
 
 // ---- packed pairs (two cells per float2, FP32 on the packed pipe) ----
@@ -435,7 +448,7 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
             const float qs_[kV + 4] = {qm2, qm1, q[0], q[1], q[2], q[3], qp4, qp5};
             const float hs_[kV + 4] = {hm2, hm1, h[0], h[1], h[2], h[3], hp4, hp5};
 #pragma unroll
-            for (int i = 0; i < kV; ++i) recon_quartic(qs_ + i, hs_ + i, b[i]);
+            for (int i = 0; i < kV; ++i) recon_quartic<LIM>(qs_ + i, hs_ + i, b[i]);
         }
         const int lo = chunk == 0 ? 0 : 2;
         const int sb = w0;

@@ -109,6 +109,8 @@ void free_device(Plan &p)
     p.row_par = nullptr;
     cudaFree(p.adj_scratch);
     p.adj_scratch = nullptr;
+    cudaFree(p.a4_scratch);
+    p.a4_scratch = nullptr;
     p.rows = nullptr;
     p.xfix = nullptr;
     p.dx32 = nullptr;
@@ -468,6 +470,11 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
     std::vector<float> dx32;
     std::vector<double> dx64;
     std::vector<int32_t> buckets;
+    // order 4 with the limiter on (the scaled quartic) runs on the general kernels:
+    // the uniform-row kernels fold a row's partial integrals into constants
+    bool limited4 = false;
+    for (int r = 0; r < nr; ++r)
+        limited4 |= p->limiter && (desc->order ? desc->order[r] : desc->default_order) == 4;
     p->rows_h.resize(nr);
     for (int r = 0; r < nr && st == RAM_OK; ++r) {
         const int n = (int)(ro[r + 1] - ro[r]);
@@ -492,7 +499,8 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
             st = RAM_ERR_MESH;
             break;
         }
-        ri.uniform = row_is_uniform(x, n) ? 1 : 0;
+        // a shared mesh serves every row, so one limited order-4 row sends them all
+        ri.uniform = (row_is_uniform(x, n) && !(limited4 && (shared || ri.order == 4))) ? 1 : 0;
         if (ri.uniform) {
             ri.mesh_off = 0;
             ri.bucket_off = 0;
@@ -529,6 +537,14 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
     }
     if (st == RAM_OK) {
         for (int r = 0; r < nr; ++r) p->n_uniform_rows += p->rows_h[r].uniform ? 1 : 0;
+        // the A4 correction is the uniform-mesh formula, on the PPM remap
+        if (desc->flags & RAM_A4) {
+            p->a4 = 1;
+            for (int r = 0; r < nr; ++r)
+                if (!p->rows_h[r].uniform || p->rows_h[r].order != 3) st = RAM_ERR_UNSUPPORTED;
+        }
+    }
+    if (st == RAM_OK) {
         if (upload(&p->rows, p->rows_h.data(), p->rows_h.size()) != cudaSuccess ||
             upload(&p->xfix, xfix.data(), xfix.size()) != cudaSuccess ||
             upload(&p->dx32, dx32.data(), dx32.size()) != cudaSuccess ||
@@ -538,6 +554,8 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
             cudaMalloc(&p->row_par, sizeof(RowParams<double>) * (size_t)nr) != cudaSuccess ||
             ((desc->flags & RAM_ADJOINT) && p->n_uniform_rows < nr &&
              cudaMalloc(&p->adj_scratch, 2 * sizeof(double) * (size_t)p->n_cells) != cudaSuccess) ||
+            ((desc->flags & RAM_A4) &&
+             cudaMalloc(&p->a4_scratch, 2 * sizeof(double) * (size_t)p->n_cells) != cudaSuccess) ||
             cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess)
             st = RAM_ERR_NOMEM;
     }

@@ -25,6 +25,7 @@ DONOR, VANLEER = 0, 1
 LIMITER_OFF = 1
 SHARED_MESH = 2
 ADJOINT = 4
+A4 = 8
 MAX_NSUB = 8
 
 EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwind",
@@ -185,7 +186,8 @@ class Plan:
     extra node per row, or the single shared mesh when shared_mesh=True."""
 
     def __init__(self, row_offset: Sequence[int], nodes, order=3, limiter: bool = True,
-                 shared_mesh: bool = False, device: int = 0, adjoint: bool = False):
+                 shared_mesh: bool = False, device: int = 0, adjoint: bool = False,
+                 a4: bool = False):
         lib = load()
         self._lib = lib
         self.row_offset = np.ascontiguousarray(row_offset, dtype=np.int64)
@@ -209,7 +211,7 @@ class Plan:
                       if self.order is not None else None)
         desc.default_order = default
         desc.flags = ((0 if limiter else LIMITER_OFF) | (SHARED_MESH if shared_mesh else 0) |
-                      (ADJOINT if adjoint else 0))
+                      (ADJOINT if adjoint else 0) | (A4 if a4 else 0))
         h = ctypes.c_void_p()
         _check(lib.ram_plan_mesh(ctypes.byref(desc), self.device, ctypes.byref(h)),
                "ram_plan_mesh")
@@ -217,10 +219,10 @@ class Plan:
 
     @classmethod
     def from_workload(cls, w, device: int = 0, limiter: Optional[bool] = None,
-                      adjoint: bool = False):
+                      adjoint: bool = False, a4: bool = False):
         return cls(w.row_offset, w.nodes, order=w.order,
                    limiter=w.limiter if limiter is None else limiter,
-                   shared_mesh=w.shared_mesh, device=device, adjoint=adjoint)
+                   shared_mesh=w.shared_mesh, device=device, adjoint=adjoint, a4=a4)
 
     def destroy(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
