@@ -59,6 +59,11 @@ def _load():
             ctypes.POINTER(ctypes.c_byte), i, d, d, ctypes.c_double, i,
             ctypes.POINTER(ctypes.c_int), d, d]
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_radial_upwind.argtypes = [i, i, d, d, d, ctypes.c_double, i, d]
+        lib.oracle_shear_dt.argtypes = [i, d, ctypes.c_double, ctypes.c_double]
+        lib.oracle_shear_dt.restype = ctypes.c_double
+        lib.oracle_step_2d.argtypes = [i, i, d, d, d, d, i, i, d, i,
+                                       ctypes.POINTER(ctypes.c_int), d, ctypes.c_double, d]
         lib.oracle_a4_average.argtypes = [i, d, d]
         lib.oracle_a4_point.argtypes = [i, d, d]
         lib.oracle_step_a4.argtypes = [i, d, d, i, ctypes.c_double, d, ctypes.c_double, i, i, d]
@@ -258,6 +263,59 @@ def step_a4(x, q, s, limiter=True, dv=None, dt=0.0, scheme=VANLEER, nsub=1,
     return (out, st) if return_status else out
 
 
+def radial_upwind(rf, q, vr, dt, scheme=VANLEER, return_status=False):
+    """Radial sweep of a polar disk (cylindrical geometry, closed ends): q and vr are
+    (rings, phi cells) and (rings + 1, phi cells) arrays, rf the ring face radii."""
+    lib = _load()
+    rf, rfp = _f64(rf)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    nr, nphi = q.shape
+    assert rf.size == nr + 1
+    vr = np.ascontiguousarray(vr, dtype=np.float64)
+    assert vr.shape == (nr + 1, nphi)
+    out = np.empty_like(q)
+    d = ctypes.POINTER(ctypes.c_double)
+    st = lib.oracle_radial_upwind(nr, nphi, rfp, q.ctypes.data_as(d), vr.ctypes.data_as(d),
+                                  float(dt), int(scheme), out.ctypes.data_as(d))
+    _check(st, allow_cfl=True)
+    return (out, st) if return_status else out
+
+
+def shear_dt(omega, dphi_min, beta):
+    """The shear limit of the split step: beta dphi_min / max |omega_{j+1} - omega_j|."""
+    lib = _load()
+    om, omp = _f64(omega)
+    return lib.oracle_shear_dt(om.size, omp, float(dphi_min), float(beta))
+
+
+def step_2d(phi, rf, omega, q, dt, order=3, limiter=True, dvphi=None, scheme=VANLEER,
+            nsub=None, vr=None):
+    """One split step of a polar disk: RAM in phi on every ring, then the radial
+    sweep (q: (rings, phi cells))."""
+    lib = _load()
+    phi, phip = _f64(phi)
+    rf, rfp = _f64(rf)
+    om, omp = _f64(omega)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    nr, nphi = q.shape
+    d = ctypes.POINTER(ctypes.c_double)
+    dvp = None
+    if dvphi is not None:
+        dvphi = np.ascontiguousarray(dvphi, dtype=np.float64)
+        dvp = dvphi.ctypes.data_as(d)
+    nsp = None
+    if nsub is not None:
+        nsub = np.ascontiguousarray(nsub, dtype=np.int32)
+        nsp = nsub.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    vr = np.zeros((nr + 1, nphi)) if vr is None else np.ascontiguousarray(vr, dtype=np.float64)
+    out = np.empty_like(q)
+    st = lib.oracle_step_2d(nr, nphi, phip, rfp, omp, q.ctypes.data_as(d), int(order),
+                            int(bool(limiter)), dvp, int(scheme), nsp, vr.ctypes.data_as(d),
+                            float(dt), out.ctypes.data_as(d))
+    _check(st, allow_cfl=True)
+    return out
+
+
 def num_threads():
     return _load().oracle_num_threads()
 
@@ -272,5 +330,5 @@ def mass(x, q):
 __all__ = ["shift", "reconstruct", "cell_cumulative", "residual", "step",
            "shift_adjoint", "residual_adjoint_donor", "step_adjoint",
            "shift_from_velocity", "phase_update", "step_rows", "num_threads", "mass",
-           "a4_average", "a4_point", "step_a4",
+           "a4_average", "a4_point", "step_a4", "radial_upwind", "shear_dt", "step_2d",
            "DONOR", "VANLEER", "OracleError"]

@@ -289,3 +289,130 @@ def bump_nodes(n: int, x_min: float, x_max: float, a: float, b: float, c: float,
     x = 0.5 * (lo + hi)
     x[0], x[-1] = x_min, x_max
     return x
+
+
+# --------------------------------------------------------------------------
+# the radial bump (App. B.2) and the two-dimensional polar disk (Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def radial_bump_density(s, s0: float, a: float, b: float, c: float):
+    """psi(s) = 1/s + c beta(|s - s0|), beta = 1 inside a, cos^2 transition to b, 0
+    outside (unnormalised)."""
+    s = np.asarray(s, dtype=np.float64)
+    t = np.abs(s - s0)
+    beta = np.where(t <= a, 1.0,
+                    np.where(t < b, np.cos(0.5 * math.pi * (t - a) / (b - a)) ** 2, 0.0))
+    return 1.0 / s + c * beta
+
+
+def radial_bump_norm(x_min: float, x_max: float, a: float, b: float, c: float) -> float:
+    """Integral of psi over [x_min, x_max] for a bump inside the domain:
+    log(x_max / x_min) + c (a + b)."""
+    return math.log(x_max) - math.log(x_min) + c * (a + b)
+
+
+def radial_bump_cumulative(x, x_min: float, x_max: float, s0: float, a: float, b: float,
+                           c: float):
+    """u(x) = (1/I) integral of psi from x_min to x, in [0, 1]."""
+    x = np.asarray(x, dtype=np.float64)
+    w = b - a
+
+    def bump_from_centre(t):
+        # integral of beta from 0 to t >= 0 (distance from s0)
+        t = np.asarray(t, dtype=np.float64)
+        tt = np.clip(t, a, b)
+        return np.minimum(t, a) + 0.5 * (tt - a) + w / (2.0 * math.pi) * np.sin(math.pi * (tt - a) / w)
+
+    def bump_prim(s):
+        d = s - s0
+        return np.sign(d) * bump_from_centre(np.abs(d))
+
+    num = np.log(x / x_min) + c * (bump_prim(x) - bump_prim(x_min))
+    return num / radial_bump_norm(x_min, x_max, a, b, c)
+
+
+def radial_bump_nodes(n: int, x_min: float, x_max: float, s0: float, a: float, b: float,
+                      c: float, iters: int = 200) -> np.ndarray:
+    """Faces with equal density integral per ring, u(r_j) = j / n, by bisection."""
+    target = np.arange(n + 1, dtype=np.float64) / n
+    lo = np.full(n + 1, x_min)
+    hi = np.full(n + 1, x_max)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        below = radial_bump_cumulative(mid, x_min, x_max, s0, a, b, c) < target
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    x = 0.5 * (lo + hi)
+    x[0], x[-1] = x_min, x_max
+    return x
+
+
+@dataclasses.dataclass
+class Disk2D:
+    """A polar disk for the dimensionally split step: rings are rows on one shared
+    azimuthal mesh `phi`; `rf` holds the n_r + 1 ring face radii."""
+    name: str
+    phi: np.ndarray        # n_phi + 1 azimuthal nodes
+    rf: np.ndarray         # n_r + 1 radial faces
+    omega: np.ndarray      # n_r angular rates of the bulk rotation (the RAM shift per time)
+    q0: np.ndarray         # (n_r, n_phi) surface density
+    dvphi: np.ndarray      # (n_r, n_phi) residual azimuthal velocity at the phi interfaces
+    vr: np.ndarray         # (n_r + 1, n_phi) radial velocity on the ring faces (0 at the ends)
+    order: int
+    limiter: bool
+    scheme: int
+    nsub: np.ndarray       # residual sub-steps per ring
+    dt: float
+
+    @property
+    def n_r(self) -> int:
+        return int(self.rf.size - 1)
+
+    @property
+    def n_phi(self) -> int:
+        return int(self.phi.size - 1)
+
+
+def polar_disk_2d(n_r: int = 128, n_phi: int = 512, seed: int = 21, nonuniform: bool = True,
+                  order: int = 2, scheme: int = 1, beta: float = 0.44,
+                  dv_amp: float = 0.01, vr_amp: float = 0.01) -> Disk2D:
+    """The mesh of Sec. 4.2: phi in [-pi, pi] on the periodic bump (a = 0.1387,
+    b = 0.2773, c = 15) and r in [0.4, 2.1] on the radial bump centred at 1 (same a,
+    b, c = 2.5), or a uniform / log-uniform mesh.  Frame co-rotating with r = 1:
+    omega = r^-3/2 - 1.  Sigma = r^-1/2 (1 + 0.1 vortex at r = 1), a seeded 1%
+    azimuthal residual velocity and a smooth seeded radial velocity that vanishes at
+    the walls.  dt is the shear limit (beta) capped by the radial and residual CFL
+    conditions."""
+    a, b = 0.1387, 0.2773
+    if nonuniform:
+        phi = bump_nodes(n_phi, -math.pi, math.pi, a, b, 15.0)
+        rf = radial_bump_nodes(n_r, 0.4, 2.1, 1.0, a, b, 2.5)
+    else:
+        phi = uniform_nodes(n_phi, -math.pi, 2.0 * math.pi)
+        rf = 0.4 * (2.1 / 0.4) ** (np.arange(n_r + 1) / n_r)
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    omega = rc ** -1.5 - 1.0
+    dphi = np.diff(phi)
+    vortex = np.exp(-((rc - 1.0) ** 2) / (2 * 0.05 ** 2))[:, None] * \
+        gaussian_averages(phi, 0.5, 0.3, 2.0 * math.pi)[None, :]
+    q0 = (rc ** -0.5)[:, None] * (1.0 + 0.1 * vortex)
+    rng = np.random.default_rng(seed)
+    dvphi = dv_amp * (rc ** -1.5)[:, None] * rng.uniform(-1.0, 1.0, (n_r, n_phi))
+    phase = rng.uniform(0.0, 2.0 * math.pi, 3)
+    pc = 0.5 * (phi[1:] + phi[:-1])
+    shape = (np.sin(pc + phase[0]) + 0.5 * np.sin(2 * pc + phase[1]))[None, :]
+    wall = ((rf - rf[0]) * (rf[-1] - rf) / ((rf[-1] - rf[0]) / 2.0) ** 2)[:, None]
+    vr = vr_amp * wall * shape
+    vr[0] = 0.0
+    vr[-1] = 0.0
+    dt_shear = beta * dphi.min() / np.max(np.abs(np.diff(omega)))
+    dr = np.diff(rf)
+    dr_face = np.minimum(np.concatenate([[np.inf], dr]), np.concatenate([dr, [np.inf]]))
+    vmax = np.max(np.abs(vr), axis=1)
+    dt_r = beta * np.min(dr_face[vmax > 0] / vmax[vmax > 0]) if np.any(vmax > 0) else np.inf
+    dt = min(dt_shear, dt_r)
+    cfl = np.abs(dvphi).max(axis=1) * dt / dphi.min()
+    nsub = np.maximum(1, np.ceil(cfl / 0.5)).astype(np.int32)
+    return Disk2D("polar_disk_2d_%dx%d%s" % (n_r, n_phi, "" if nonuniform else "_uniform"),
+                  phi, rf, omega, np.ascontiguousarray(q0), np.ascontiguousarray(dvphi),
+                  np.ascontiguousarray(vr), order, True, scheme, nsub, float(dt))

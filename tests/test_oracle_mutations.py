@@ -57,6 +57,14 @@ MUTANTS = {
     "limited4_blend": ("g = th * g + (1.0 - th) * r->q[i] * d;",
                        "g = th * g + (1.0 - th) * r->q[i] * r->dx[i];"),
     "limited4_theta": ("double t = (hi - Q) / (qmax - Q);", "double t = (hi - Q) / (qmax + Q);"),
+    "radial_face_length": ("dt * (rf[j + 1] * F[j + 1] - rf[j] * F[j]) / area;",
+                           "dt * (F[j + 1] - F[j]) / area;"),
+    "radial_ring_area": ("double area = 0.5 * (rf[j + 1] * rf[j + 1] - rf[j] * rf[j]);",
+                         "double area = 0.5 * (rf[j + 1] + rf[j]) * (rf[j + 1] - rf[j]) * 1.01;"),
+    "radial_upwind_side": ("qh = col[j - 1] + sig[j - 1] * 0.5 * (dr[j - 1] - c);",
+                           "qh = col[j] + sig[j - 1] * 0.5 * (dr[j - 1] - c);"),
+    "shear_difference_sign": ("double d = fabs(omega[j + 1] - omega[j]);",
+                              "double d = omega[j + 1] - omega[j];"),
 }
 
 

@@ -743,3 +743,109 @@ def test_limited_order4_no_new_extrema_and_conservation():
     assert ql.max() <= 1.0 + 1e-12 and ql.min() >= -1e-12
     assert qu.max() > 1.0 + 1e-3 or qu.min() < -1e-3
     assert abs(oracle.mass(x, ql) - oracle.mass(x, q0)) <= 1e-13 * oracle.mass(x, q0)
+
+
+# ---------------------------------------------------------------------------
+# two dimensions by dimensional splitting (Sec. 3.5), the radial bump (App. B.2)
+# ---------------------------------------------------------------------------
+
+def _ring_areas(rf):
+    return 0.5 * (rf[1:] ** 2 - rf[:-1] ** 2)
+
+
+@pytest.mark.parametrize("scheme", [oracle.DONOR, oracle.VANLEER])
+def test_radial_sweep_conserves_mass(scheme):
+    """Closed radial walls: sum over rings of q times ring area is conserved."""
+    rf = wl.radial_bump_nodes(40, 0.4, 2.1, 1.0, 0.1387, 0.2773, 2.5)
+    rng = np.random.default_rng(1)
+    q = 1.0 + rng.random((40, 16))
+    vr = 0.2 * (rng.random((41, 16)) - 0.5) * np.diff(rf).min()
+    vr[0] = vr[-1] = 0.0
+    out = oracle.radial_upwind(rf, q, vr, 1.0, scheme)
+    area = _ring_areas(rf)
+    np.testing.assert_allclose((out * area[:, None]).sum(axis=0), (q * area[:, None]).sum(axis=0),
+                               rtol=1e-14)
+
+
+def test_radial_sweep_divergence_free_flow_keeps_a_constant():
+    """r vr constant on the interior faces: the flux divergence vanishes in every ring
+    that has two open faces, so a constant density stays constant there (cylindrical
+    geometry; a planar update would not)."""
+    rf = np.linspace(0.5, 2.0, 31)
+    q = np.full((30, 4), 2.5)
+    vr = np.zeros((31, 4))
+    vr[1:-1] = 0.01 / rf[1:-1, None]
+    for scheme in (oracle.DONOR, oracle.VANLEER):
+        out = oracle.radial_upwind(rf, q, vr, 0.7, scheme)
+        np.testing.assert_allclose(out[1:-1], 2.5, rtol=1e-14)
+        assert out[0, 0] < 2.5 and out[-1, 0] > 2.5  # the walls stop the flow
+
+
+def test_radial_sweep_planar_limit_is_a_shift():
+    """Far from the axis (thin annulus) a donor sweep at Courant number 1 with r vr
+    constant moves every ring's value to the next ring, to O(dr / r)."""
+    n = 20
+    r0 = 1.0e6
+    rf = r0 + np.arange(n + 1, dtype=np.float64)
+    q = np.random.default_rng(2).random((n, 3))
+    vr = np.zeros((n + 1, 3))
+    vr[1:-1] = r0 / rf[1:-1, None]  # ~1: one ring width per unit time
+    out = oracle.radial_upwind(rf, q, vr, 1.0, oracle.DONOR)
+    np.testing.assert_allclose(out[1:-1], q[:-2], atol=1e-4)
+
+
+def test_radial_sweep_donor_positive_and_cfl_flag():
+    rf = np.linspace(0.4, 2.1, 25)
+    rng = np.random.default_rng(3)
+    q = rng.random((24, 8))
+    vr = (rng.random((25, 8)) - 0.5) * 2.0 * np.diff(rf).min()
+    vr[0] = vr[-1] = 0.0
+    out, st = oracle.radial_upwind(rf, q, vr, 0.45, oracle.DONOR, return_status=True)
+    assert st == 0 and out.min() >= 0.0
+    _, st = oracle.radial_upwind(rf, q, vr * 4.0, 1.0, oracle.DONOR, return_status=True)
+    assert st == 3
+
+
+def test_shear_limit_bounds_the_relative_shift_of_neighbouring_rings():
+    """With the shear limit, no two neighbouring rings move apart by more than beta
+    azimuthal cells in one step, and one pair does by exactly that."""
+    rf = wl.radial_bump_nodes(64, 0.4, 2.1, 1.0, 0.1387, 0.2773, 2.5)
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    omega = rc ** -1.5 - 1.0
+    dphi = 2 * np.pi / 300
+    dt = oracle.shear_dt(omega, dphi, 0.44)
+    rel = np.abs(np.diff(omega)) * dt
+    assert rel.max() <= 0.44 * dphi * (1 + 1e-14)
+    assert abs(rel.max() - 0.44 * dphi) <= 1e-14 * dphi
+    assert oracle.shear_dt(np.full(5, 0.7), dphi, 0.44) == np.inf
+
+
+def test_radial_bump_mesh():
+    """App. B.2: the normalisation I = log(x_max / x_min) + c (a + b) by quadrature,
+    the faces' density integrals equal, and c = 0 gives the log-uniform mesh."""
+    import scipy.integrate as si
+    a, b, c = 0.1387, 0.2773, 2.5
+    I_q, _ = si.quad(lambda s: wl.radial_bump_density(s, 1.0, a, b, c), 0.4, 2.1,
+                     points=[1 - b, 1 - a, 1 + a, 1 + b], limit=200)
+    assert abs(I_q - wl.radial_bump_norm(0.4, 2.1, a, b, c)) <= 1e-12 * I_q
+    rf = wl.radial_bump_nodes(50, 0.4, 2.1, 1.0, a, b, c)
+    pieces = [si.quad(lambda s: wl.radial_bump_density(s, 1.0, a, b, c), rf[j], rf[j + 1],
+                      epsabs=0.0, epsrel=1e-13, limit=200)[0] for j in range(50)]
+    np.testing.assert_allclose(pieces, I_q / 50, rtol=1e-9)
+    logu = wl.radial_bump_nodes(16, 0.4, 2.1, 1.0, a, b, 0.0)
+    np.testing.assert_allclose(logu, 0.4 * (2.1 / 0.4) ** (np.arange(17) / 16), rtol=1e-13)
+
+
+def test_split_step_is_the_ring_steps_then_the_radial_sweep():
+    """The split step with no radial flow is the RAM step of every ring; with no
+    rotation and no residual it is the radial sweep alone."""
+    d = wl.polar_disk_2d(n_r=12, n_phi=64)
+    rows = np.stack([oracle.step(d.phi, d.q0[j], oracle.shift_from_velocity(d.omega[j], d.dt),
+                                 d.order, True, d.dvphi[j], d.dt, d.scheme, int(d.nsub[j]))
+                     for j in range(12)])
+    got = oracle.step_2d(d.phi, d.rf, d.omega, d.q0, d.dt, d.order, True, d.dvphi, d.scheme,
+                         d.nsub, np.zeros_like(d.vr))
+    np.testing.assert_array_equal(got, rows)
+    got = oracle.step_2d(d.phi, d.rf, np.zeros(12), d.q0, d.dt, d.order, True, None, d.scheme,
+                         None, d.vr)
+    np.testing.assert_array_equal(got, oracle.radial_upwind(d.rf, d.q0, d.vr, d.dt, d.scheme))
