@@ -150,6 +150,25 @@ ram_status ram_step_adjoint(ram_plan plan, ram_dtype dtype, const void *q_in,
                             const void *dv_iface, void *g_dv, const int32_t *nsub,
                             void *stream);
 
+/* The radial sweep of a polar disk, for dimensional splitting in two dimensions
+ * (Sec. 3.5: RAM along the azimuth, a standard upwind step along the radius).  The
+ * plan must have RAM_SHARED_MESH (RAM_ERR_UNSUPPORTED otherwise): its rows are the
+ * rings j = 0 .. n_rows-1 of N azimuthal cells on one mesh, ring j between the
+ * radii rf[j] < rf[j+1] (rf: device, FP64, n_rows + 1 values, increasing).
+ * vr: device, the plan's dtype, (n_rows + 1) x N values, element j N + i is the
+ * radial velocity on face j (radius rf[j], between rings j-1 and j) at azimuthal
+ * cell i; faces 0 and n_rows are closed walls and are not read.  One flux-form
+ * upwind step of length dt in cylindrical geometry:
+ *   q'_j = q_j - dt (rf[j+1] F_{j+1} - rf[j] F_j) / A_j,  A_j = (rf[j+1]^2 - rf[j]^2) / 2,
+ * F = vr q_up (RAM_DONOR) or vr times the upwind ring's van Leer profile (Sec. 3.1,
+ * centre spacings; flat in the rings next to the walls) at the midpoint of the
+ * swept interval (RAM_VANLEER).  Conserves sum_j A_j q_j over every column.
+ * |vr| dt above the upwind ring's width sets RAM_ERR_CFL in the error word.
+ * Enqueues one kernel; no allocation or synchronisation. */
+ram_status ram_radial_upwind(ram_plan plan, ram_dtype dtype, const void *q_in, void *q_out,
+                             const double *rf, const void *vr, double dt, ram_scheme scheme,
+                             void *stream);
+
 /* Mass of every row, sum_i Q_i dx_i (Eq. 10), written as FP64 to mass_out
  * (device, one per row).  FP32 cells are summed exactly as products and
  * accumulated with a compensated (two-float) scan. */

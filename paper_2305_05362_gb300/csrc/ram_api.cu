@@ -220,3 +220,20 @@ extern "C" ram_status ram_row_mass(ram_plan plan, ram_dtype dtype, const void *q
     cudaError_t e = launch_row_mass(*p, dtype, q, mass_out, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? RAM_OK : RAM_ERR_CUDA;
 }
+
+extern "C" ram_status ram_radial_upwind(ram_plan plan, ram_dtype dtype, const void *q_in,
+                                        void *q_out, const double *rf, const void *vr,
+                                        double dt, ram_scheme scheme, void *stream)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    ram_status st = check_common(p, dtype, q_in, q_out);
+    if (st != RAM_OK) return st;
+    if (!rf || !vr || (scheme != RAM_DONOR && scheme != RAM_VANLEER)) return RAM_ERR_ARG;
+    if (!(dt >= 0.0) || dt > 1e300) return RAM_ERR_ARG;
+    if (!(p->flags & RAM_SHARED_MESH)) return RAM_ERR_UNSUPPORTED;  // rings of one mesh
+    DeviceGuard g(p->device);
+    if (!g.ok) return RAM_ERR_CUDA;
+    cudaError_t e = launch_radial(*p, dtype, q_in, q_out, rf, vr, dt, scheme,
+                                  static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RAM_OK : RAM_ERR_CUDA;
+}

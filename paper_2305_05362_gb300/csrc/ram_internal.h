@@ -238,6 +238,10 @@ cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const
 // corrected averages, else the inverse
 cudaError_t launch_a4(const Plan &p, ram_dtype dt, const void *in, void *out, cudaStream_t s,
                       bool to_avg);
+// the radial sweep of a polar disk (ram_radial.cu)
+cudaError_t launch_radial(const Plan &p, ram_dtype dt, const void *q_in, void *q_out,
+                          const double *rf, const void *vr, double step, int scheme,
+                          cudaStream_t s);
 // rows with their own mesh (ram_adjoint_nu.cu)
 cudaError_t launch_adjoint_nu(const Plan &p, ram_dtype dt, const StepArgs &a, const void *g_out,
                               void *g_in, void *g_dv, cudaStream_t s);

@@ -32,6 +32,7 @@ EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwin
            "ram_step", "ram_step_adjoint", "ram_row_mass", "ram_plan_check_errors",
            "ram_plan_query", "ram_plan_set_tiling", "ram_plan_set_wait_limit",
            "ram_plan_get_tuning", "ram_plan_set_tuning", "ram_plan_autotune", "ram_step_uniform_noalloc",
+           "ram_radial_upwind",
            "ram_status_string", "ram_version"]
 STATIC_MAX_ROWS = 4096
 
@@ -104,6 +105,7 @@ def load(path: Optional[str] = None):
     lib.ram_plan_autotune.argtypes = [vp, i32, vp, vp, vp, f64, vp, i32, vp, i32, vp]
     lib.ram_step_uniform_noalloc.argtypes = [i32, i32, i32, f64, i32, ctypes.c_uint32, vp, vp,
                                              vp, f64, vp, i32, vp, vp, vp]
+    lib.ram_radial_upwind.argtypes = [vp, i32, vp, vp, vp, vp, f64, i32, vp]
     lib.ram_status_string.argtypes = [i32]
     lib.ram_status_string.restype = ctypes.c_char_p
     lib.ram_version.restype = i32
@@ -368,6 +370,45 @@ def step_uniform_noalloc(q_in, q_out, n_rows: int, period: float, order: int, v0
                                             int(scheme), _ptr(nsub), _ptr(device_errors),
                                             _stream(dev.index, stream)),
                "ram_step_uniform_noalloc")
+
+
+def radial_upwind(plan: Plan, q_in, q_out, rf, vr, dt: float, scheme: int = VANLEER,
+                  stream=None):
+    """ram_radial_upwind: one radial flux-form upwind step of a polar disk whose rings
+    are the plan's rows (shared azimuthal mesh); rf: FP64 ring faces (n_rows + 1), vr:
+    radial velocity on the faces, (n_rows + 1) x N in q's dtype."""
+    import torch
+    dev = _plan_device(plan)
+    _need(q_in, "q_in", plan.n_cells, device=dev)
+    _dtype_code(q_in)
+    _need(q_out, "q_out", plan.n_cells, q_in.dtype, dev)
+    _need(rf, "rf", plan.n_rows + 1, torch.float64, dev)
+    _need(vr, "vr", plan.n_cells + plan.n_cells // plan.n_rows, q_in.dtype, dev)
+    _check(plan._lib.ram_radial_upwind(plan.handle, _dtype_code(q_in), _ptr(q_in), _ptr(q_out),
+                                       _ptr(rf), _ptr(vr), float(dt), int(scheme),
+                                       _stream(plan.device, stream)), "ram_radial_upwind")
+
+
+def shear_dt(omega, dphi_min: float, beta: float = 0.44) -> float:
+    """The shear limit of the split step: the largest dt for which neighbouring rings
+    turning at the angular rates omega shear by at most beta times the smallest
+    azimuthal cell, beta dphi_min / max |omega_{j+1} - omega_j| (host arithmetic)."""
+    om = np.asarray(omega, dtype=np.float64)
+    m = float(np.max(np.abs(np.diff(om)))) if om.size > 1 else 0.0
+    return beta * float(dphi_min) / m if m > 0.0 else float("inf")
+
+
+def step_2d(plan: Plan, q_in, q_out, omega, dt: float, rf, vr, dvphi=None,
+            scheme: int = VANLEER, nsub=None, scratch=None, phase=None, stream=None):
+    """One dimensionally split step of a polar disk (Sec. 3.5): the RAM step of every
+    ring (shift by omega dt along the azimuth, residual dvphi), then the radial sweep.
+    `scratch` (q's shape and dtype) holds the intermediate field; allocated when
+    not given."""
+    import torch
+    mid = torch.empty_like(q_in) if scratch is None else scratch
+    step(plan, q_in, mid, omega, dt, dv=dvphi, scheme=scheme, nsub=nsub, phase=phase,
+         stream=stream)
+    radial_upwind(plan, mid, q_out, rf, vr, dt, scheme=scheme, stream=stream)
 
 
 def version() -> int:

@@ -103,3 +103,14 @@ def test_noalloc_refusals():
                                      device_errors=args["device_errors"])
     with pytest.raises(ValueError):
         ram.step_uniform_noalloc(q, out, 0, 1.0, 3, v0, 0.1)
+
+
+def test_shear_dt_host_helper_matches_the_oracle():
+    import numpy as np
+    import oracle
+    from paper_2305_05362_gb300 import workloads as wl
+    rf = wl.radial_bump_nodes(80, 0.4, 2.1, 1.0, 0.1387, 0.2773, 2.5)
+    rc = 0.5 * (rf[1:] + rf[:-1])
+    om = rc ** -1.5 - 1.0
+    assert ram.shear_dt(om, 0.013, 0.44) == oracle.shear_dt(om, 0.013, 0.44)
+    assert ram.shear_dt(np.ones(4), 0.013) == float("inf")
