@@ -102,6 +102,25 @@ typedef struct {
  * On failure *out is NULL and nothing is leaked. */
 ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_plan *out);
 
+/* A row generated by a mesh-density function: the periodic bump of App. B.1,
+ * density 1 + c for |x| <= a, 1 + c cos^2(pi/2 (|x| - a)/(b - a)) for a < |x| < b,
+ * 1 beyond, on the row's domain [x_min, x_max] (which holds the bump: x_min <= -b,
+ * b <= x_max), normalised by I = (x_max - x_min) + c (a + b) (Eq. 24). */
+typedef struct {
+    double x_min, x_max;
+    double a, b, c;
+} ram_density;
+
+/* Mark rows as generated by their mesh-density function, so that the kernels
+ * locate shifted edges with the index function of Sec. 3.2.1, p = floor(N u(x~))
+ * with u the normalised cumulative of the density in closed form (App. B.1),
+ * corrected against the row's exact nodes, instead of the plan's bucket table.
+ * dens: host, one entry per row (with RAM_SHARED_MESH: one entry), or NULL to go
+ * back to the bucket tables.  Each row's nodes must be the density's: x_0 = x_min,
+ * x_N = x_max and |N u(x_j) - j| <= 1/4 at every node (RAM_ERR_MESH otherwise, the
+ * plan unchanged).  Uniform rows ignore it.  Host synchronous, allocates. */
+ram_status ram_plan_set_density(ram_plan plan, const ram_density *dens);
+
 /* Free every device and host resource of the plan (the device copy of the
  * Sec. 2 mesh, the Sec. 3.2.1 index tables and the tile lists built by
  * ram_plan_mesh).  Host synchronous; NULL is accepted.  The caller's current
@@ -204,6 +223,7 @@ typedef struct {
     int32_t device;
     int32_t n_nseg_rows;      /* rows with their own mesh that FP32 steps run on the
                                  warp-segment kernel (the others take the tiled one) */
+    int32_t n_density_rows;   /* rows located by their mesh-density function */
 } ram_plan_info;
 
 ram_status ram_plan_query(ram_plan plan, ram_plan_info *info);

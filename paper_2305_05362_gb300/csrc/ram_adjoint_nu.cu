@@ -36,15 +36,6 @@ constexpr int kAH = 3;  // halo of the reconstruction transpose, cells per side
 __device__ __forceinline__ float u64f(uint64_t v, float) { return __ull2float_rn(v); }
 __device__ __forceinline__ double u64f(uint64_t v, double) { return __ull2double_rn(v); }
 
-// the output cell holding a position (fixed point) of a row: bucket table and walk
-__device__ __forceinline__ int locate_nu(const uint64_t *X, int n, const int32_t *bt, int bits,
-                                         uint64_t y)
-{
-    int p = bt[y >> (64 - bits)];
-    while (p + 1 < n && X[p + 1] <= y) ++p;
-    return p;
-}
-
 // Order 4: the mean of the two quartics' Lagrange weights at offset xi (units of
 // the cell width h) on the node offsets z[0..5] (z[2] = 0, z[3] = 1), folded into
 // the weights of the five masses m_{p-2..p+2}: G = sum_j w_j m_{p-2+j}.
@@ -118,7 +109,7 @@ __global__ void __launch_bounds__(256)
         const uint64_t y0 = X[p] + S;                       // shifted left node
         const uint64_t wp = (p + 1 < N ? X[p + 1] : 0ull) - X[p];  // width (fixed point)
         const T h = sdx[j];
-        int i = locate_nu(X, N, bt, row.bucket_bits, y0);
+        int i = locate_cell(X, N, bt, row.bucket_bits, a.density, row.density, y0);
         T lo = T(0);
         T nu[5] = {0, 0, 0, 0, 0};
         T z[6];

@@ -59,6 +59,7 @@ StepArgs base_args(const Plan *p, const void *q_in, void *q_out)
     a.dx32 = p->dx32;
     a.dx64 = p->dx64;
     a.buckets = p->buckets;
+    a.density = p->density;
     a.wait_limit = p->wait_limit;
     return a;
 }

@@ -438,6 +438,47 @@ __device__ __forceinline__ T quartic_scaling_theta(T a1, T a2, T a3, T a4, T Q, 
     return fmax(th, T(0));
 }
 
+// The index function of Sec. 3.2.1 for a row generated by a mesh-density function
+// (App. B.1, the periodic bump): the nodes satisfy u(x_j) = j / N with u the
+// normalised cumulative of the density, so the cell holding x is floor(N u(x)).
+// u is evaluated in FP32 from its closed form; the caller corrects the guess
+// against the row's exact nodes (at most a step or two).
+__device__ __forceinline__ int density_index(const Density &d, int n, uint64_t y)
+{
+    const float x = d.x_min + d.L * ((float)(y >> 40) * 0x1p-24f);  // position of y
+    const float t = fabsf(x);
+    const float w = d.b - d.a;
+    const float tt = fminf(fmaxf(t, d.a), d.b);
+    // integral of the unnormalised density from 0 to |x|, signed
+    float pr = (1.f + d.c) * fminf(t, d.a) + (tt - d.a) +
+               d.c * (0.5f * (tt - d.a) + w * (0.5f / 3.14159265358979f) *
+                                              __sinf(3.14159265358979f * (tt - d.a) / w)) +
+               fmaxf(t - d.b, 0.f);
+    pr = x < 0.f ? -pr : pr;
+    const float u = (pr - d.prim_min) * d.inv_norm;
+    const int p = (int)floorf(u * (float)n);
+    return p < 0 ? 0 : (p >= n ? n - 1 : p);
+}
+
+// The source cell p of a row with x_p <= y < x_{p+1} (Eq. 16), y a position as a
+// fraction of the period in units of 2^-64 (the nodes X likewise, X[0] = 0): a
+// first guess from the index function of the row's density when it has one,
+// else from the plan's bucket table (the index function tabulated on the row's
+// own nodes), then a walk along the exact nodes.
+__device__ __forceinline__ int locate_cell(const uint64_t *X, int n, const int32_t *bt, int bits,
+                                           const Density *dens, int di, uint64_t y)
+{
+    int p;
+    if (di >= 0) {
+        p = density_index(dens[di], n, y);
+        while (p > 0 && X[p] > y) --p;
+    } else {
+        p = bt[y >> (64 - bits)];
+    }
+    while (p + 1 < n && X[p + 1] <= y) ++p;
+    return p;
+}
+
 // Wait until the kernels this one depends on (programmatic dependent launch)
 // have finished and their writes are visible; a no-op for a normal launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

@@ -259,16 +259,6 @@ __device__ T cell_G(const T *q, const T *dx, int p, T xi, bool lim)
 __device__ __forceinline__ float u64_to(uint64_t v, float) { return __ull2float_rn(v); }
 __device__ __forceinline__ double u64_to(uint64_t v, double) { return __ull2double_rn(v); }
 
-// the source cell holding a shifted position (fixed point), from the bucket table
-// and a short walk along the row's nodes (Eq. 16, Sec. 3.2.1)
-__device__ __forceinline__ int locate_row(const uint64_t *X, int n, const int32_t *bt, int bits,
-                                          uint64_t y)
-{
-    int p = bt[y >> (64 - bits)];
-    while (p + 1 < n && X[p + 1] <= y) ++p;
-    return p;
-}
-
 template <typename T>
 __device__ __forceinline__ T vl_slope_nu(const T *c, const T *w, int u)
 {
@@ -378,7 +368,7 @@ __global__ void __launch_bounds__(512)
             if (tid < 2) {
                 const int e = tid == 0 ? wrap_index((int64_t)tile.start - H, N)
                                        : wrap_index((int64_t)tile.start + T_out + H, N);
-                p = locate_row(X, N, bt, row.bucket_bits, X[e] - S);
+                p = locate_cell(X, N, bt, row.bucket_bits, a.density, row.density, X[e] - S);
             }
             const int phi = __shfl_sync(0xffffffffu, p, 1);
             plo = p;
@@ -572,7 +562,7 @@ __global__ void __launch_bounds__(512)
             const int e = en < N ? en : en - N;
             const uint64_t y = X[e] - S;
             if (k == 0 || y < yprev) {
-                p = locate_row(X, N, bt, row.bucket_bits, y);
+                p = locate_cell(X, N, bt, row.bucket_bits, a.density, row.density, y);
             } else {
                 while (p + 1 < N && X[p + 1] <= y) ++p;
             }

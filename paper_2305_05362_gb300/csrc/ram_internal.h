@@ -32,11 +32,19 @@ struct RowInfo {
     int32_t bucket_bits;  // log2 of the row's bucket count
     int32_t qshift;       // FP32 warp-segment kernel: window-relative fixed-point
                           // positions are kept as 32-bit values in units of 2^qshift
-    int32_t pad;
+    int32_t density;      // index of the row's mesh-density function, -1: none
     double period;        // L
     double cells_per_length;  // N / L
     double dx;            // L / N (uniform rows)
     double inv_period;    // 1 / L
+};
+
+// A row's mesh-density function (App. B.1, the periodic bump centred at 0 on
+// [x_min, x_min + L]), for the index function of Sec. 3.2.1.
+struct Density {
+    float x_min, L, a, b, c, inv_norm;  // inv_norm = 1 / (L + c (a + b))
+    float prim_min;                       // the bump's primitive at x_min
+    float pad;
 };
 
 // Position of a row in the packed arrays, for kernels that stage whole rows.
@@ -97,6 +105,7 @@ struct StepArgs {
     const float *dx32;      // widths, FP32
     const double *dx64;     // widths, FP64
     const int32_t *buckets; // per-row bucket table: cell holding each bucket start
+    const Density *density; // mesh-density functions of rows that have one
     uint32_t wait_limit = kWaitLimit;  // tries of every bounded mbarrier wait
     int32_t row_phase = 0;  // no parameter kernel ran: the row kernels advance the phase
 };
@@ -196,6 +205,7 @@ struct Plan {
     float *dx32 = nullptr;
     double *dx64 = nullptr;
     int32_t *buckets = nullptr;
+    Density *density = nullptr;
     int *err = nullptr;
 };
 

@@ -61,7 +61,7 @@ __global__ void k_static_rows(RowInfo *rows, int32_t *ids, int n_rows, int n, do
     ri.uniform = 1;
     ri.bucket_bits = 0;
     ri.qshift = 0;
-    ri.pad = 0;
+    ri.density = -1;
     ri.period = period;
     ri.cells_per_length = (double)n / period;
     ri.dx = period / n;

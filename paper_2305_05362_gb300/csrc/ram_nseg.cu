@@ -644,8 +644,7 @@ __global__ void __launch_bounds__(kNsegWarps * 32, 3)
     int p = 0;
     const uint64_t y = xe - S;
     if (locator) {
-        p = bt[y >> (64 - row.bucket_bits)];
-        while (p + 1 < N && X[p + 1] <= y) ++p;
+        p = locate_cell(X, N, bt, row.bucket_bits, a.density, row.density, y);
     }
 
     const NLayout Lo = nseg_layout(RESID);

@@ -104,6 +104,8 @@ void free_device(Plan &p)
     cudaFree(p.dx32);
     cudaFree(p.dx64);
     cudaFree(p.buckets);
+    cudaFree(p.density);
+    p.density = nullptr;
     cudaFree(p.err);
     cudaFree(p.row_par);
     p.row_par = nullptr;
@@ -480,6 +482,7 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
         const int n = (int)(ro[r + 1] - ro[r]);
         const double *x = shared ? p->nodes_h.data() : p->nodes_h.data() + ro[r] + r;
         RowInfo &ri = p->rows_h[r];
+        ri.density = -1;
         ri.cell_off = ro[r];
         ri.n = n;
         ri.order = desc->order ? desc->order[r] : desc->default_order;
@@ -603,6 +606,9 @@ extern "C" ram_status ram_plan_query(ram_plan plan, ram_plan_info *info)
     info->threads = p->threads;
     info->device = p->device;
     info->n_nseg_rows = p->nseg_rows;
+    int nd = 0;
+    for (const RowInfo &ri : p->rows_h) nd += ri.density >= 0 ? 1 : 0;
+    info->n_density_rows = nd;
     return RAM_OK;
 }
 
@@ -685,3 +691,86 @@ extern "C" const char *ram_status_string(ram_status s)
 }
 
 extern "C" int32_t ram_version(void) { return 100; }
+
+namespace {
+
+// integral from 0 to x of the unnormalised periodic-bump density (signed)
+double bump_primitive(const ram_density &d, double x)
+{
+    const double t = std::fabs(x), w = d.b - d.a;
+    const double tt = std::min(std::max(t, d.a), d.b);
+    const double pr = (1.0 + d.c) * std::min(t, d.a) + (tt - d.a) +
+                      d.c * (0.5 * (tt - d.a) + w / (2.0 * M_PI) * std::sin(M_PI * (tt - d.a) / w)) +
+                      std::max(t - d.b, 0.0);
+    return x < 0.0 ? -pr : pr;
+}
+
+}  // namespace
+
+extern "C" ram_status ram_plan_set_density(ram_plan plan, const ram_density *dens)
+{
+    if (!plan) return RAM_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    const bool shared = (p->flags & RAM_SHARED_MESH) != 0;
+    std::vector<Density> table;
+    std::vector<int32_t> index(p->n_rows, -1);
+    if (dens) {
+        for (int r = 0; r < p->n_rows; ++r) {
+            const RowInfo &ri = p->rows_h[r];
+            if (ri.uniform) continue;
+            const ram_density &d = dens[shared ? 0 : r];
+            if (!(d.a > 0.0) || !(d.b > d.a) || !(d.c > -1.0) || !std::isfinite(d.c) ||
+                !(d.x_max > d.x_min) || d.x_min > -d.b || d.x_max < d.b)
+                return RAM_ERR_ARG;
+            const int n = ri.n;
+            const double *x = shared ? p->nodes_h.data() : p->nodes_h.data() + p->row_offset[r] + r;
+            const double L = d.x_max - d.x_min;
+            const double inv = 1.0 / (L + d.c * (d.a + d.b));
+            const double pm = bump_primitive(d, d.x_min);
+            if (std::fabs(x[0] - d.x_min) > 1e-12 * L || std::fabs(x[n] - d.x_max) > 1e-12 * L)
+                return RAM_ERR_MESH;
+            for (int j = 0; j <= n; ++j)
+                if (std::fabs(n * (bump_primitive(d, x[j]) - pm) * inv - j) > 0.25)
+                    return RAM_ERR_MESH;
+            if (shared && r > 0) {
+                index[r] = index[0];
+                continue;
+            }
+            Density e;
+            e.x_min = (float)d.x_min;
+            e.L = (float)L;
+            e.a = (float)d.a;
+            e.b = (float)d.b;
+            e.c = (float)d.c;
+            e.inv_norm = (float)inv;
+            e.prim_min = (float)pm;
+            e.pad = 0.f;
+            index[r] = (int32_t)table.size();
+            table.push_back(e);
+        }
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(p->device) != cudaSuccess) return RAM_ERR_CUDA;
+    ram_status st = RAM_OK;
+    Density *dev = nullptr;
+    if (cudaDeviceSynchronize() != cudaSuccess || upload(&dev, table.data(), table.size()) != cudaSuccess)
+        st = RAM_ERR_NOMEM;
+    if (st == RAM_OK) {
+        std::vector<RowInfo> rows = p->rows_h;
+        for (int r = 0; r < p->n_rows; ++r) rows[r].density = index[r];
+        if (cudaMemcpy(p->rows, rows.data(), sizeof(RowInfo) * rows.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            st = RAM_ERR_CUDA;
+            cudaFree(dev);
+        } else {
+            p->rows_h = rows;
+            cudaFree(p->density);
+            p->density = dev;
+        }
+    } else {
+        cudaFree(dev);
+    }
+    cudaSetDevice(prev);
+    return st;
+}

@@ -32,7 +32,7 @@ EXPORTS = ["ram_plan_mesh", "ram_plan_destroy", "ram_shift", "ram_residual_upwin
            "ram_step", "ram_step_adjoint", "ram_row_mass", "ram_plan_check_errors",
            "ram_plan_query", "ram_plan_set_tiling", "ram_plan_set_wait_limit",
            "ram_plan_get_tuning", "ram_plan_set_tuning", "ram_plan_autotune", "ram_step_uniform_noalloc",
-           "ram_radial_upwind",
+           "ram_radial_upwind", "ram_plan_set_density",
            "ram_status_string", "ram_version"]
 STATIC_MAX_ROWS = 4096
 
@@ -41,6 +41,12 @@ class RamError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = status
         super().__init__("%s: %s (%d)" % (where, STATUS.get(status, "?"), status))
+
+
+class Density(ctypes.Structure):
+    """ram_density: the periodic bump of App. B.1 on [x_min, x_max]."""
+    _fields_ = [("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double)]
 
 
 class _MeshDesc(ctypes.Structure):
@@ -57,7 +63,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_uniform_rows", ctypes.c_int32), ("n_tiles_uniform", ctypes.c_int32),
                 ("n_tiles_general", ctypes.c_int32), ("tile_cells", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("n_nseg_rows", ctypes.c_int32)]
+                ("n_nseg_rows", ctypes.c_int32), ("n_density_rows", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -106,6 +112,7 @@ def load(path: Optional[str] = None):
     lib.ram_step_uniform_noalloc.argtypes = [i32, i32, i32, f64, i32, ctypes.c_uint32, vp, vp,
                                              vp, f64, vp, i32, vp, vp, vp]
     lib.ram_radial_upwind.argtypes = [vp, i32, vp, vp, vp, vp, f64, i32, vp]
+    lib.ram_plan_set_density.argtypes = [vp, ctypes.POINTER(Density)]
     lib.ram_status_string.argtypes = [i32]
     lib.ram_status_string.restype = ctypes.c_char_p
     lib.ram_version.restype = i32
@@ -261,6 +268,16 @@ class Plan:
     def set_tuning(self, t: Tuning):
         _check(self._lib.ram_plan_set_tuning(self.handle, ctypes.byref(t)),
                "ram_plan_set_tuning")
+
+    def set_density(self, densities):
+        """ram_plan_set_density: locate the edges of rows generated by the periodic
+        bump (App. B.1) with the index function of Sec. 3.2.1.  `densities`: one
+        (x_min, x_max, a, b, c) per row (one for a shared mesh), or None."""
+        if densities is None:
+            _check(self._lib.ram_plan_set_density(self.handle, None), "ram_plan_set_density")
+            return
+        arr = (Density * len(densities))(*[Density(*map(float, d)) for d in densities])
+        _check(self._lib.ram_plan_set_density(self.handle, arr), "ram_plan_set_density")
 
     def set_wait_limit(self, limit: int = 1 << 20):
         """Tries of every bounded device-side wait (test hook; 0: give up at once,

@@ -124,3 +124,73 @@ def test_fig2_on_gpu(dtype):
                 slope = np.polyfit(np.log(ns), np.log(errs[o]), 1)[0]
                 assert abs(slope - target) <= tol, (kind, profile, o, slope)
             assert all(a > b for a, b in zip(errs[2], errs[3])), (kind, profile)
+
+
+def _densities(cases):
+    """The periodic bump of every bump row (App. B.1); uniform rows take none."""
+    lo, hi = FIG2["setup"]["domain"]
+    b = FIG2["setup"]["bump_mesh"]
+    return [(lo, hi, b["a"], b["a"] + b["b_minus_a"], b["c"]) for _ in cases]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nseg", [False, True])
+def test_fig2_with_the_index_function(dtype, nseg):
+    """The same runs with the bump rows located by the index function of Sec. 3.2.1
+    (p = floor(N u(x~)) from the closed-form cumulative, App. B.1) instead of the
+    plan's bucket table: the located cells are exact either way, so the fields are
+    identical bit for bit, and the printed slopes hold."""
+    if nseg and dtype == torch.float64:
+        pytest.skip("the warp-segment kernel is FP32")
+    cases = _cases()
+    xs = [_mesh(kind, n) for kind, _, _, n in cases]
+    q0s = [_q0(x, profile) for x, (_, profile, _, _) in zip(xs, cases)]
+    lens = [x.size - 1 for x in xs]
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    sh, n_steps = _schedule(xs)
+    shd = torch.tensor(sh, dtype=torch.float64, device=DEV)
+    finals = []
+    for with_density in (False, True):
+        plan = ram.Plan(ro, np.concatenate(xs), order=np.array([c[2] for c in cases], np.int8),
+                        limiter=True)
+        if nseg:
+            t = plan.tuning()
+            t.nonuniform_kernel_f32 = 1
+            plan.set_tuning(t)
+        if with_density:
+            plan.set_density(_densities(cases))
+            n_bump = sum(1 for c in cases if c[0] == "bump")
+            assert plan.info().n_density_rows == n_bump
+        q = torch.tensor(np.concatenate(q0s), dtype=dtype, device=DEV)
+        buf = torch.empty_like(q)
+        for k in range(sh.shape[0]):
+            ram.shift(plan, q, buf, shd[k])
+            q, buf = buf, q
+        torch.cuda.synchronize()
+        assert plan.check_errors() == 0
+        finals.append(q.double().cpu().numpy())
+    assert np.array_equal(finals[0], finals[1])
+    got = finals[1]
+    e1 = {}
+    for r, ((kind, profile, order, n), x, q0) in enumerate(zip(cases, xs, q0s)):
+        g = got[ro[r]:ro[r + 1]]
+        e1[(kind, profile, order, n)] = float(np.sum(np.abs(g - q0) * np.diff(x)) / np.sum(np.diff(x)))
+    ns = FIG2["setup"]["N"]
+    for profile in ("smooth", "square"):
+        target = FIG2["printed"]["%s_slope" % profile]
+        tol = FIG2["tolerance"]["%s_slope" % profile]
+        for o in (2, 3):
+            slope = np.polyfit(np.log(ns), np.log([e1[("bump", profile, o, n)] for n in ns]), 1)[0]
+            assert abs(slope - target) <= tol, (profile, o, slope)
+
+
+def test_density_refused_for_other_nodes():
+    """Nodes that are not the density's are refused (RAM_ERR_MESH), the plan unchanged."""
+    n = 64
+    lo, hi = FIG2["setup"]["domain"]
+    b = FIG2["setup"]["bump_mesh"]
+    plan = ram.Plan([0, n], wl.random_nodes(n, seed=3, x0=lo, length=hi - lo), order=3)
+    with pytest.raises(ram.RamError) as e:
+        plan.set_density([(lo, hi, b["a"], b["a"] + b["b_minus_a"], b["c"])])
+    assert e.value.status == 2
+    assert plan.info().n_density_rows == 0
