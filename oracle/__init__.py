@@ -64,6 +64,10 @@ def _load():
         lib.oracle_shear_dt.restype = ctypes.c_double
         lib.oracle_step_2d.argtypes = [i, i, d, d, d, d, i, i, d, i,
                                        ctypes.POINTER(ctypes.c_int), d, ctypes.c_double, d]
+        lib.oracle_shift_jvp.argtypes = [i, d, d, i, i, ctypes.c_double, d, d]
+        lib.oracle_shift_vjp.argtypes = [i, d, d, i, i, ctypes.c_double, d, d]
+        lib.oracle_step_adjoint_limited.argtypes = [i, d, d, i, i, ctypes.c_double, d,
+                                                    ctypes.c_double, i, d, d, d]
         lib.oracle_a4_average.argtypes = [i, d, d]
         lib.oracle_a4_point.argtypes = [i, d, d]
         lib.oracle_step_a4.argtypes = [i, d, d, i, ctypes.c_double, d, ctypes.c_double, i, i, d]
@@ -316,6 +320,47 @@ def step_2d(phi, rf, omega, q, dt, order=3, limiter=True, dvphi=None, scheme=VAN
     return out
 
 
+def shift_jvp(x, q0, v, s, order=3, limiter=True):
+    """The shift's derivative at q0 along v (the limiters' branches as q0 decides)."""
+    lib = _load()
+    x, xp = _f64(x)
+    q0, qp = _f64(q0)
+    v, vp = _f64(v)
+    out, op = _f64(np.empty(q0.size))
+    _check(lib.oracle_shift_jvp(q0.size, xp, qp, int(order), int(bool(limiter)), float(s), vp, op))
+    return out
+
+
+def shift_vjp(x, q0, g, s, order=3, limiter=True):
+    """The transpose of shift_jvp applied to g (small rows: one tangent per cell)."""
+    lib = _load()
+    x, xp = _f64(x)
+    q0, qp = _f64(q0)
+    g, gp = _f64(g)
+    out, op = _f64(np.empty(q0.size))
+    _check(lib.oracle_shift_vjp(q0.size, xp, qp, int(order), int(bool(limiter)), float(s), gp, op))
+    return out
+
+
+def step_adjoint_limited(x, q_in, g_out, s, order=3, limiter=True, dv=None, dt=0.0, nsub=1):
+    """Transpose of the step linearised at q_in (PLM / PPM shift, donor residual);
+    returns (g_in, g_dv)."""
+    lib = _load()
+    x, xp = _f64(x)
+    q, qp = _f64(q_in)
+    g, gp = _f64(g_out)
+    gi, gip = _f64(np.empty(q.size))
+    if dv is None:
+        dvp = None
+        gdv, gdvp = None, None
+    else:
+        dv, dvp = _f64(dv)
+        gdv, gdvp = _f64(np.zeros(q.size))
+    _check(lib.oracle_step_adjoint_limited(q.size, xp, qp, int(order), int(bool(limiter)),
+                                           float(s), dvp, float(dt), int(nsub), gp, gip, gdvp))
+    return gi, gdv
+
+
 def num_threads():
     return _load().oracle_num_threads()
 
@@ -331,4 +376,5 @@ __all__ = ["shift", "reconstruct", "cell_cumulative", "residual", "step",
            "shift_adjoint", "residual_adjoint_donor", "step_adjoint",
            "shift_from_velocity", "phase_update", "step_rows", "num_threads", "mass",
            "a4_average", "a4_point", "step_a4", "radial_upwind", "shear_dt", "step_2d",
+           "shift_jvp", "shift_vjp", "step_adjoint_limited",
            "DONOR", "VANLEER", "OracleError"]

@@ -1080,6 +1080,223 @@ int oracle_residual_adjoint_donor(int n, const double *x, const double *q_in,
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Linearisation of the limited step at a forward state                         */
+/* ------------------------------------------------------------------------- */
+
+/* The tangent (directional derivative) of the shift at q0 along v, for PLM and PPM
+ * with or without the limiter: every quantity of the reconstruction is carried as
+ * a value and its derivative, and every branch of the limiters (App. A.2, the van
+ * Leer slope) is taken as the value decides it -- the linearisation at the
+ * forward state.  The remap (Eq. 18) is linear in the reconstruction for fixed
+ * edges, so its tangent is the same formula on the derivatives. */
+typedef struct {
+    double v, d;
+} dual_t;
+
+static dual_t dmk(double v, double d)
+{
+    dual_t r = {v, d};
+    return r;
+}
+static dual_t dadd(dual_t a, dual_t b) { return dmk(a.v + b.v, a.d + b.d); }
+static dual_t dsub(dual_t a, dual_t b) { return dmk(a.v - b.v, a.d - b.d); }
+static dual_t dmul(dual_t a, dual_t b) { return dmk(a.v * b.v, a.d * b.v + a.v * b.d); }
+static dual_t dscale(dual_t a, double s) { return dmk(a.v * s, a.d * s); }
+static dual_t ddiv(dual_t a, dual_t b)
+{
+    return dmk(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+
+int oracle_shift_jvp(int n, const double *x, const double *q0, int order, int limiter,
+                     double s, const double *vdir, double *out)
+{
+    if (n < 1 || (order != 2 && order != 3)) return ORC_ERR_ARG;
+    recon_t r;
+    int st = recon_build(&r, n, x, q0, order, limiter); /* widths and the edge geometry */
+    if (st) {
+        recon_free(&r);
+        return st;
+    }
+    const double *dx = r.dx;
+    dual_t *q = (dual_t *)malloc(sizeof(dual_t) * (size_t)n);
+    dual_t *c0 = (dual_t *)malloc(sizeof(dual_t) * (size_t)n);
+    dual_t *c1 = (dual_t *)malloc(sizeof(dual_t) * (size_t)n);
+    dual_t *c2 = (dual_t *)malloc(sizeof(dual_t) * (size_t)n);
+    for (int i = 0; i < n; ++i) q[i] = dmk(q0[i], vdir[i]);
+    if (order == 2) {
+        for (int i = 0; i < n; ++i) {
+            int im = cyc(i - 1, n), ip = cyc(i + 1, n);
+            double hl = 0.5 * (dx[im] + dx[i]), hr = 0.5 * (dx[i] + dx[ip]);
+            dual_t sig;
+            if (limiter) {
+                dual_t dl = dscale(dsub(q[i], q[im]), 1.0 / hl);
+                dual_t dr = dscale(dsub(q[ip], q[i]), 1.0 / hr);
+                if (dl.v * dr.v <= 0.0)
+                    sig = dmk(0.0, 0.0);
+                else
+                    sig = ddiv(dscale(dmul(dl, dr), 2.0), dadd(dl, dr));
+            } else {
+                sig = dscale(dsub(q[ip], q[im]), 1.0 / (hl + hr));
+            }
+            c0[i] = q[i];
+            c1[i] = sig;
+        }
+    } else {
+        dual_t *dq = (dual_t *)malloc(sizeof(dual_t) * (size_t)n);
+        dual_t *face = (dual_t *)malloc(sizeof(dual_t) * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+            int im = cyc(i - 1, n), ip = cyc(i + 1, n);
+            double a = dx[im], b = dx[i], c = dx[ip];
+            dual_t up = dsub(q[ip], q[i]), dn = dsub(q[i], q[im]);
+            dual_t d = dadd(dscale(up, b / (a + b + c) * (2.0 * a + b) / (b + c)),
+                            dscale(dn, b / (a + b + c) * (b + 2.0 * c) / (a + b)));
+            if (limiter) {
+                if (up.v * dn.v > 0.0) {
+                    /* sign(d) min(|d|, 2|dn|, 2|up|), the smallest taken by value */
+                    dual_t m = d.v >= 0.0 ? d : dscale(d, -1.0);
+                    dual_t an = dscale(dn.v >= 0.0 ? dn : dscale(dn, -1.0), 2.0);
+                    dual_t au = dscale(up.v >= 0.0 ? up : dscale(up, -1.0), 2.0);
+                    if (an.v < m.v) m = an;
+                    if (au.v < m.v) m = au;
+                    d = d.v >= 0.0 ? m : dscale(m, -1.0);
+                } else {
+                    d = dmk(0.0, 0.0);
+                }
+            }
+            dq[i] = d;
+        }
+        for (int i = 0; i < n; ++i) {
+            int im = cyc(i - 1, n), ip = cyc(i + 1, n), ip2 = cyc(i + 2, n);
+            double hm = dx[im], h0 = dx[i], h1 = dx[ip], h2 = dx[ip2];
+            double w1 = 2.0 * h1 * h0 / (h0 + h1) *
+                        ((hm + h0) / (2.0 * h0 + h1) - (h2 + h1) / (2.0 * h1 + h0));
+            double w2 = -h0 * (hm + h0) / (2.0 * h0 + h1);
+            double w3 = h1 * (h1 + h2) / (h0 + 2.0 * h1);
+            double sum4 = hm + h0 + h1 + h2;
+            dual_t del = dsub(q[ip], q[i]);
+            face[i] = dadd(dadd(q[i], dscale(del, h0 / (h0 + h1))),
+                           dscale(dadd(dadd(dscale(del, w1), dscale(dq[ip], w2)), dscale(dq[i], w3)),
+                                  1.0 / sum4));
+        }
+        for (int i = 0; i < n; ++i) {
+            dual_t L = face[cyc(i - 1, n)], R = face[i], Q = q[i];
+            if (limiter) {
+                if ((R.v - Q.v) * (Q.v - L.v) <= 0.0) {
+                    L = Q;
+                    R = Q;
+                } else {
+                    double dd = R.v - L.v, qa = Q.v - 0.5 * (L.v + R.v);
+                    if (dd * qa > dd * dd / 6.0)
+                        L = dsub(dscale(Q, 3.0), dscale(R, 2.0));
+                    else if (-dd * dd / 6.0 > dd * qa)
+                        R = dsub(dscale(Q, 3.0), dscale(L, 2.0));
+                }
+            }
+            c0[i] = L;
+            c1[i] = R;
+            c2[i] = dsub(dscale(Q, 6.0), dscale(dadd(L, R), 3.0));
+        }
+        free(dq);
+        free(face);
+    }
+    /* the remap of the derivatives: the forward formulas with d in place of v */
+    recon_t t = r;
+    double *d0 = (double *)malloc(sizeof(double) * (size_t)n);
+    double *d1 = (double *)malloc(sizeof(double) * (size_t)n);
+    double *d2 = (double *)calloc((size_t)n, sizeof(double));
+    double *dm = (double *)malloc(sizeof(double) * (size_t)n);
+    double *dqv = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        d0[i] = c0[i].d;
+        d1[i] = c1[i].d;
+        if (order == 3) d2[i] = c2[i].d;
+        dqv[i] = vdir[i];
+        dm[i] = vdir[i] * dx[i];
+    }
+    t.c0 = d0;
+    t.c1 = d1;
+    t.c2 = d2;
+    t.m = dm;
+    t.q = dqv;
+    t.limited = 0;
+    double L = x[n] - x[0];
+    edges_t e;
+    edges_build(&e, n, x, reduce_shift(s, L));
+    for (int i = 0; i < n; ++i) {
+        cover_t c;
+        cover_cell(n, dx, e.p, e.y, e.d, i, &c);
+        if (c.copy) {
+            out[i] = vdir[c.pl];
+            continue;
+        }
+        double mass;
+        if (c.same) {
+            mass = cell_G(&t, c.pl, c.dr) - cell_G(&t, c.pl, c.dl);
+        } else {
+            mass = t.m[c.pl] - cell_G(&t, c.pl, c.dl);
+            for (int k = 1; k <= c.nwhole; ++k) mass += t.m[cyc(c.pl + k, n)];
+            mass += cell_G(&t, c.pr, c.dr);
+        }
+        out[i] = mass / dx[i];
+    }
+    edges_free(&e);
+    free(d0);
+    free(d1);
+    free(d2);
+    free(dm);
+    free(dqv);
+    free(q);
+    free(c0);
+    free(c1);
+    free(c2);
+    recon_free(&r);
+    return ORC_OK;
+}
+
+/* The transpose of that tangent, by its definition: (J^T g)_k = <J e_k, g>, one
+ * tangent per cell (small rows only: quadratic cost). */
+int oracle_shift_vjp(int n, const double *x, const double *q0, int order, int limiter,
+                     double s, const double *g, double *out)
+{
+    double *e = (double *)calloc((size_t)n, sizeof(double));
+    double *col = (double *)malloc(sizeof(double) * (size_t)n);
+    int st = ORC_OK;
+    for (int k = 0; k < n && !st; ++k) {
+        e[k] = 1.0;
+        st = oracle_shift_jvp(n, x, q0, order, limiter, s, e, col);
+        e[k] = 0.0;
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) acc += col[i] * g[i];
+        out[k] = acc;
+    }
+    free(e);
+    free(col);
+    return st;
+}
+
+/* Transpose of the step linearised at q_in: the shift (PLM / PPM, the limiter as
+ * the plan has it) linearised at q_in, then the donor residual (linear).  g_dv as
+ * in oracle_step_adjoint. */
+int oracle_step_adjoint_limited(int n, const double *x, const double *q_in, int order,
+                                int limiter, double s, const double *dv, double dt, int nsub,
+                                const double *g_out, double *g_in, double *g_dv)
+{
+    double *qs = (double *)malloc(sizeof(double) * (size_t)n);
+    double *gs = (double *)malloc(sizeof(double) * (size_t)n);
+    int st = oracle_shift(n, x, q_in, order, limiter, s, qs);
+    if (!st) {
+        if (dv)
+            st = oracle_residual_adjoint_donor(n, x, qs, dv, dt, nsub, g_out, gs, g_dv);
+        else
+            memcpy(gs, g_out, sizeof(double) * (size_t)n);
+    }
+    if (!st) st = oracle_shift_vjp(n, x, q_in, order, limiter, s, gs, g_in);
+    free(qs);
+    free(gs);
+    return st;
+}
+
 /* Transpose of one linear RAM step (limiter-off shift, donor residual): given
  * the step input q_in and the cotangent of the output, produce the cotangent of
  * the input and add d loss / d dv into g_dv (may be NULL). dv may be NULL. */

@@ -65,6 +65,12 @@ MUTANTS = {
                            "qh = col[j] + sig[j - 1] * 0.5 * (dr[j - 1] - c);"),
     "shear_difference_sign": ("double d = fabs(omega[j + 1] - omega[j]);",
                               "double d = omega[j + 1] - omega[j];"),
+    "tangent_minmod_choice": ("if (an.v < m.v) m = an;", "if (an.v > m.v) m = an;"),
+    "tangent_vanleer_factor": ("sig = ddiv(dscale(dmul(dl, dr), 2.0), dadd(dl, dr));",
+                               "sig = ddiv(dscale(dmul(dl, dr), 1.0), dadd(dl, dr));"),
+    "tangent_constraint_operand": ("L = dsub(dscale(Q, 3.0), dscale(R, 2.0));",
+                                   "L = dsub(dscale(Q, 3.0), dscale(L, 2.0));"),
+    "tangent_mass_derivative": ("dm[i] = vdir[i] * dx[i];", "dm[i] = vdir[i];"),
 }
 
 

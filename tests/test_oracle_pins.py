@@ -849,3 +849,73 @@ def test_split_step_is_the_ring_steps_then_the_radial_sweep():
     got = oracle.step_2d(d.phi, d.rf, np.zeros(12), d.q0, d.dt, d.order, True, None, d.scheme,
                          None, d.vr)
     np.testing.assert_array_equal(got, oracle.radial_upwind(d.rf, d.q0, d.vr, d.dt, d.scheme))
+
+
+# ---------------------------------------------------------------------------
+# the step linearised at a forward state (limited PLM / PPM)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_linearisation_without_limiter_is_the_linear_transpose(order):
+    """With the limiter off the step is linear: the transpose of the tangent equals
+    the hand-derived transpose of the linear step."""
+    x = wl.random_nodes(48, seed=100 + order)
+    rng = np.random.default_rng(order)
+    q0, g = 1.0 + rng.random(48), rng.standard_normal(48)
+    np.testing.assert_allclose(oracle.shift_vjp(x, q0, g, 0.417, order, False),
+                               oracle.shift_adjoint(x, g, 0.417, order), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_limited_ppm_tangent_is_exact_within_its_branches(seed):
+    """The limited PPM is piecewise linear in Q (App. A.2 selects among linear
+    expressions): along a direction small enough to keep every branch, the step's
+    increment is exactly the tangent times the step length."""
+    x = wl.random_nodes(64, seed=110 + seed)
+    rng = np.random.default_rng(seed)
+    q0 = wl.three_gaussians(x, seed) + 0.3 * rng.random(64)
+    v = rng.standard_normal(64)
+    eps = 1e-7
+    jv = oracle.shift_jvp(x, q0, v, 0.3713, 3, True)
+    inc = (oracle.shift(x, q0 + eps * v, 0.3713, 3, True) - oracle.shift(x, q0, 0.3713, 3, True)) / eps
+    assert np.max(np.abs(inc - jv)) <= 1e-6 * np.max(np.abs(jv))
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_limited_tangent_against_central_differences(order):
+    x = wl.random_nodes(50, seed=120 + order)
+    rng = np.random.default_rng(120 + order)
+    q0 = 1.0 + rng.random(50)
+    for s in (0.011, 0.77, -2.3):
+        v = rng.standard_normal(50)
+        h = 1e-6
+        fd = (oracle.shift(x, q0 + h * v, s, order, True) - oracle.shift(x, q0 - h * v, s, order, True)) / (2 * h)
+        jv = oracle.shift_jvp(x, q0, v, s, order, True)
+        assert np.max(np.abs(fd - jv)) <= 1e-6 * np.max(np.abs(jv)), s
+
+
+def test_limited_step_adjoint_dot_product_and_dv_gradient():
+    """The step linearised at q (limited PPM shift, donor residual): <g, R J v> =
+    <J^T R^T g, v> with the donor residual R linear in its input, and d<g, step>/d dv
+    against central differences."""
+    n = 40
+    x = wl.random_nodes(n, seed=130)
+    rng = np.random.default_rng(131)
+    q = wl.three_gaussians(x, 132)
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    dv = sign * (0.3 + 0.5 * rng.random(n)) * np.diff(x).min()
+    dt, s, nsub = 0.5, 0.2217, 2
+    g = rng.standard_normal(n)
+    gi, gdv = oracle.step_adjoint_limited(x, q, g, s, 3, True, dv, dt, nsub)
+    v = rng.standard_normal(n)
+    rjv = oracle.residual(x, oracle.shift_jvp(x, q, v, s, 3, True), dv, dt, oracle.DONOR, nsub)
+    assert abs(g @ rjv - gi @ v) <= 1e-12 * (np.abs(g) @ np.abs(rjv))
+
+    def loss(d):
+        return float(g @ oracle.step(x, q, s, 3, True, d, dt, oracle.DONOR, nsub))
+
+    h = 1e-6 * np.diff(x).min()
+    for k in range(5):
+        e = rng.standard_normal(n)
+        fd = (loss(dv + h * e) - loss(dv - h * e)) / (2 * h)
+        assert fd == pytest.approx(float(gdv @ e), rel=1e-6, abs=1e-9)
