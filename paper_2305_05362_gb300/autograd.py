@@ -1,9 +1,12 @@
 """Differentiable RAM steps on top of the C ABI.
 
-RamSegment runs k steps forward with ram_step (limiter-off plan, donor residual:
-the step is linear in Q, Sec. 3 with Eq. 6) and, in backward, recomputes the k
-forward states from its saved input and walks back through them with
-ram_step_adjoint, accumulating the gradient of the residual velocity.
+RamSegment runs k steps forward with ram_step (donor residual) and, in backward,
+recomputes the k forward states from its saved input and walks back through them
+with ram_step_adjoint, accumulating the gradient of the residual velocity.  With
+the limiter off the step is linear in Q (Sec. 3 with Eq. 6) and the backward pass
+is its exact transpose; with the limiter on (a plan built with adjoint=True) each
+step is linearised at its own input, the limiter branches frozen where that input
+puts them, which is the gradient wherever the step is differentiable.
 rollout() chains segments, so memory holds one checkpoint per segment
 (checkpoint-and-recompute every k steps).
 """
@@ -52,8 +55,8 @@ class RamSegment(torch.autograd.Function):
 def rollout(plan, q0, v0, dt: float, steps: int, dv=None, nsub=None,
             checkpoint_every: int = 20):
     """Advance q0 by `steps` RAM steps, differentiable with respect to q0 and dv.
-    The plan must be built with limiter=False (the transpose needs a linear step),
-    and with adjoint=True when it has rows with their own mesh and dv is given."""
+    The plan needs adjoint=True when its limiter is on, and when it has rows with
+    their own mesh and dv is given."""
     q = q0
     done = 0
     while done < steps:

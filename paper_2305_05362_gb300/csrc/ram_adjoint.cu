@@ -237,6 +237,8 @@ cudaError_t launch_adjoint(const Plan &p, ram_dtype dt, const StepArgs &a, const
     // rows with their own mesh and a residual step need the plan's scratch
     const bool nonuni = p.n_uniform_rows < p.n_rows;
     if (nonuni && a.dv != nullptr && p.adj_scratch == nullptr) return cudaErrorNotSupported;
+    // a limited plan: every row on the gather adjoint, linearised at the step input
+    if (p.adj_all) return launch_adjoint_nu(p, dt, a, g_out, g_in, g_dv, s);
     cudaError_t e = launch_params(p, dt, a, s);
     if (e != cudaSuccess) return e;
     if (dt == RAM_F32) {

@@ -1,5 +1,6 @@
-// Transpose of one linear RAM step (limiter off, donor residual) on rows with
-// their own mesh.
+// Transpose of one RAM step on rows with their own mesh (limiter off: the linear
+// step; RAM_ADJOINT plans with the limiter on: every row, the PLM / PPM step
+// linearised at its input), donor residual.
 //
 // The remap with the limiter off is linear: output mass M'_i (Eq. 18) is the sum
 // over the source cells p that the shifted output cell overlaps of
@@ -62,16 +63,143 @@ __device__ __forceinline__ void quartic_mass_weights(const T z[6], T xi, T w[5])
     w[4] = l[5];
 }
 
+// A value with its derivatives along the five stencil values Q_{p-2..p+2}.
+template <typename T> struct D5 {
+    T v, d[5];
+};
+template <typename T> __device__ __forceinline__ D5<T> d5(T v, int seed)
+{
+    D5<T> r;
+    r.v = v;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.d[k] = T(k == seed ? 1 : 0);
+    return r;
+}
+template <typename T> __device__ __forceinline__ D5<T> d5add(const D5<T> &a, const D5<T> &b, T sb = T(1))
+{
+    D5<T> r;
+    r.v = a.v + sb * b.v;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.d[k] = a.d[k] + sb * b.d[k];
+    return r;
+}
+template <typename T> __device__ __forceinline__ D5<T> d5scale(const D5<T> &a, T s)
+{
+    D5<T> r;
+    r.v = a.v * s;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.d[k] = a.d[k] * s;
+    return r;
+}
+template <typename T> __device__ __forceinline__ D5<T> d5mul(const D5<T> &a, const D5<T> &b)
+{
+    D5<T> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+template <typename T> __device__ __forceinline__ D5<T> d5div(const D5<T> &a, const D5<T> &b)
+{
+    D5<T> r;
+    const T ib = Num<T>::div(T(1), b.v);
+    r.v = a.v * ib;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+    return r;
+}
+
+// The contribution w[k] of source cell p to g_in at cell p-2+k: the cotangents nu
+// of its cumulative's power-basis coefficients (G = sum_k b_k xi^(k+1)) times the
+// coefficients' derivatives along Q_{p-2..p+2}, for the limited PLM (Sec. 3.1) or
+// PPM (App. A, App. A.2) linearised at the stencil values qs (every limiter branch
+// taken as the values decide).  hs: the stencil widths.
+template <typename T, int ORDER>
+__device__ __forceinline__ void limited_block(const T qs[5], const T hs[5], const T nu[3], T w[5])
+{
+    D5<T> Q[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Q[k] = d5<T>(qs[k], k);
+    const T h = hs[2];
+    D5<T> b[3];
+    if (ORDER == 2) {
+        const T hl = T(0.5) * (hs[1] + hs[2]), hr = T(0.5) * (hs[2] + hs[3]);
+        const D5<T> dl = d5scale(d5add(Q[2], Q[1], T(-1)), Num<T>::div(T(1), hl));
+        const D5<T> dr = d5scale(d5add(Q[3], Q[2], T(-1)), Num<T>::div(T(1), hr));
+        D5<T> sig = d5<T>(T(0), -1);
+        if (dl.v * dr.v > T(0)) sig = d5div(d5scale(d5mul(dl, dr), T(2)), d5add(dl, dr));
+        b[0] = d5scale(d5add(Q[2], sig, T(-0.5) * h), h);  // h (Q - sigma h / 2)
+        b[1] = d5scale(sig, T(0.5) * h * h);                // h^2 sigma / 2
+        b[2] = d5<T>(T(0), -1);
+    } else {
+        D5<T> dq[3];  // delta<Q> of cells p-1, p, p+1 (stencil 1, 2, 3)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int k = c + 1;
+            const T a = hs[k - 1], bb = hs[k], cc = hs[k + 1];
+            const T f = Num<T>::div(bb, a + bb + cc);
+            const D5<T> up = d5add(Q[k + 1], Q[k], T(-1)), dn = d5add(Q[k], Q[k - 1], T(-1));
+            D5<T> d = d5add(d5scale(up, f * Num<T>::div(T(2) * a + bb, bb + cc)), dn,
+                            f * Num<T>::div(bb + T(2) * cc, a + bb));
+            if (up.v * dn.v > T(0)) {
+                // sign(d) min(|d|, 2|dn|, 2|up|), the smallest taken by value
+                const T sd = d.v >= T(0) ? T(1) : T(-1);
+                D5<T> m = d5scale(d, sd);
+                const D5<T> an = d5scale(dn, dn.v >= T(0) ? T(2) : T(-2));
+                const D5<T> au = d5scale(up, up.v >= T(0) ? T(2) : T(-2));
+                if (an.v < m.v) m = an;
+                if (au.v < m.v) m = au;
+                d = d5scale(m, sd);
+            } else {
+                d = d5<T>(T(0), -1);
+            }
+            dq[c] = d;
+        }
+        D5<T> face[2];  // faces p - 1/2 (k = 1) and p + 1/2 (k = 2)
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const int k = f + 1;
+            const T hm = hs[k - 1], h0 = hs[k], h1 = hs[k + 1], h2 = hs[k + 2];
+            const T w1 = Num<T>::div(T(2) * h1 * h0, h0 + h1) *
+                         (Num<T>::div(hm + h0, T(2) * h0 + h1) - Num<T>::div(h2 + h1, T(2) * h1 + h0));
+            const T w2 = -h0 * Num<T>::div(hm + h0, T(2) * h0 + h1);
+            const T w3 = h1 * Num<T>::div(h1 + h2, h0 + T(2) * h1);
+            const T is4 = Num<T>::div(T(1), hm + h0 + h1 + h2);
+            const T cq = Num<T>::div(h0, h0 + h1) + w1 * is4;
+            const D5<T> del = d5add(Q[k + 1], Q[k], T(-1));
+            face[f] = d5add(d5add(d5add(Q[k], del, cq), dq[f + 1], w2 * is4), dq[f], w3 * is4);
+        }
+        D5<T> L = face[0], R = face[1];
+        const D5<T> &Qc = Q[2];
+        if ((R.v - Qc.v) * (Qc.v - L.v) <= T(0)) {
+            L = Qc;
+            R = Qc;
+        } else {
+            const T dd = R.v - L.v, qa = Qc.v - T(0.5) * (L.v + R.v);
+            if (dd * qa > dd * dd * (T(1) / T(6)))
+                L = d5add(d5scale(Qc, T(3)), R, T(-2));
+            else if (-dd * dd * (T(1) / T(6)) > dd * qa)
+                R = d5add(d5scale(Qc, T(3)), L, T(-2));
+        }
+        const D5<T> Q6 = d5add(d5scale(Qc, T(6)), d5add(L, R), T(-3));
+        b[0] = d5scale(L, h);
+        b[1] = d5scale(d5add(d5add(R, L, T(-1)), Q6), T(0.5) * h);
+        b[2] = d5scale(Q6, -h * (T(1) / T(3)));
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = nu[0] * b[0].d[k] + nu[1] * b[1].d[k] + nu[2] * b[2].d[k];
+}
+
 // Shared-memory layout of the remap transpose for a tile of tn source cells.
 template <typename T> struct ALayout {
     static __host__ __device__ size_t bytes(int tn)
     {
         const int m = tn + 2 * kAH;
-        return sizeof(T) * (size_t)(6 * m + 16);
+        return sizeof(T) * (size_t)(7 * m + 24);
     }
 };
 
-template <typename T, int ORDER>
+template <typename T, int ORDER, bool LIM>
 __global__ void __launch_bounds__(256)
     k_adj_remap_nu(StepArgs a, const RowParams<T> *pars, const T *gprime, T *g_in, int tcap)
 {
@@ -85,6 +213,8 @@ __global__ void __launch_bounds__(256)
     T *s2 = s1 + m;
     T *s3 = s2 + m;
     T *s4 = s3 + m;
+    T *sq0_raw = s4 + m;  // limited: the step input on the widths' cells
+    T *sq0 = sq0_raw + 2;
 
     const Tile tile = a.tiles[blockIdx.x];
     const RowInfo row = a.rows[tile.row];
@@ -99,8 +229,12 @@ __global__ void __launch_bounds__(256)
     const uint64_t S = pars[tile.row].sfix;
     const int a0 = tile.start, tn = tile.count;
     const int nm = tn + 2 * kAH;  // cells a0-3 .. a0+tn+3
-    for (int j = tid; j < nm + 5; j += nth)
-        sdx_raw[j] = DX[wrap_index((int64_t)a0 - kAH - 2 + j, N)];
+    const T *q0 = static_cast<const T *>(a.q_in) + row.cell_off;
+    for (int j = tid; j < nm + 5; j += nth) {
+        const int c = wrap_index((int64_t)a0 - kAH - 2 + j, N);
+        sdx_raw[j] = DX[c];
+        if (LIM) sq0_raw[j] = q0[c];
+    }
     __syncthreads();
 
     // ---- nu of every source cell of the tile and its halo ----
@@ -150,7 +284,23 @@ __global__ void __launch_bounds__(256)
             lo = hi;
             i = i + 1 < N ? i + 1 : 0;
         }
-        if (ORDER == 2) {
+        if (LIM) {
+            // the limited reconstruction linearised at the step input: this cell's
+            // contributions to g_in at cells p-2 .. p+2
+            T qs[5], hs[5], w[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                qs[k] = sq0[j - 2 + k];
+                hs[k] = sdx[j - 2 + k];
+            }
+            const T nu3[3] = {nu[0], nu[1], nu[2]};
+            limited_block<T, ORDER == 2 ? 2 : 3>(qs, hs, nu3, w);
+            sq[j] = w[0];
+            s1[j] = w[1];
+            s2[j] = w[2];
+            s3[j] = w[3];
+            s4[j] = w[4];
+        } else if (ORDER == 2) {
             // G = h [xi Q + sh (xi^2 - xi) / 2], sh = 2 (Q+ - Q-) h / (h- + 2h + h+)
             const T hm = sdx[j - 1], hp = sdx[j + 1];
             sq[j] = h * nu[0];                                          // d/dQ_p
@@ -168,8 +318,16 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
 
-    // ---- the reconstruction's transpose (limiter off) over the stencil ----
+    // ---- the reconstruction's transpose over the stencil ----
     T *gi = g_in + row.cell_off;
+    if (LIM) {
+        // cell m gathers w[k] of cells p = m + 2 - k
+        for (int t = tid; t < tn; t += nth) {
+            const int j = t + kAH;
+            gi[a0 + t] = sq[j + 2] + s1[j + 1] + s2[j] + s3[j - 1] + s4[j - 2];
+        }
+        return;
+    }
     if (ORDER == 2) {
         // g_m = dQ_m + t_{m-1} - t_{m+1}, t = d/d sh * d sh/d Q+
         for (int t = tid; t < tn; t += nth) {
@@ -263,7 +421,7 @@ __global__ void __launch_bounds__(256)
     pdl_wait();
     const RowParams<T> P = pars[tile.row];
     const int ns = P.nsub;
-    const T h = P.cf;  // sub-step length dt / nsub
+    const T h = (T)(a.dt / (double)(ns > 0 ? ns : 1));  // sub-step length dt / nsub
     const int a0 = tile.start, tn = tile.count;
     const int c0 = a0 - ns;  // first cell of the halo
     const int nc = tn + 2 * ns;
@@ -321,7 +479,7 @@ __global__ void __launch_bounds__(256)
     for (int i = tid; i < tn; i += nth) gpo[a0 + i] = cur[ns + i];
 }
 
-template <typename T, int ORDER>
+template <typename T, int ORDER, bool LIM>
 cudaError_t launch_adj_remap_nu(const Plan &p, const StepArgs &a, const void *gp, void *g_in,
                                 cudaStream_t s)
 {
@@ -329,13 +487,13 @@ cudaError_t launch_adj_remap_nu(const Plan &p, const StepArgs &a, const void *gp
     if (n == 0) return cudaSuccess;
     const int tcap = p.adj_nu_tcap;
     const size_t smem = ALayout<T>::bytes(tcap);
-    cudaError_t e = cudaFuncSetAttribute(k_adj_remap_nu<T, ORDER>,
+    cudaError_t e = cudaFuncSetAttribute(k_adj_remap_nu<T, ORDER, LIM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     StepArgs b = a;
     b.tiles = p.tiles_adj_nu[ORDER];
     b.n_tiles = n;
-    return launch_pdl(k_adj_remap_nu<T, ORDER>, n, 256, smem, s, b,
+    return launch_pdl(k_adj_remap_nu<T, ORDER, LIM>, n, 256, smem, s, b,
                       static_cast<const RowParams<T> *>(p.row_par), static_cast<const T *>(gp),
                       static_cast<T *>(g_in), tcap);
 }
@@ -355,7 +513,18 @@ cudaError_t launch_adj_nu_t(const Plan &p, const StepArgs &a, const void *g_out,
         StepArgs f = a;
         f.q_out = qs;
         f.dv = nullptr;
-        cudaError_t e = launch_general(p, sizeof(T) == 4 ? RAM_F32 : RAM_F64, f, s);
+        const ram_dtype dt = sizeof(T) == 4 ? RAM_F32 : RAM_F64;
+        cudaError_t e = cudaSuccess;
+        if (p.adj_all) {
+            // every row: the shift's own parameters (no residual), the uniform and
+            // the general kernels, then the step's parameters back for the transposes
+            e = launch_params(p, dt, f, s);
+            if (e == cudaSuccess) e = launch_uniform(p, dt, f, s);
+            if (e == cudaSuccess) e = launch_general(p, dt, f, s);
+            if (e == cudaSuccess) e = launch_params(p, dt, a, s);
+        } else {
+            e = launch_general(p, dt, f, s);
+        }
         if (e != cudaSuccess) return e;
         const int tcap = p.adj_nu_tcap;
         const int wc = tcap + 2 * RAM_MAX_NSUB + 2;
@@ -387,10 +556,19 @@ cudaError_t launch_adj_nu_t(const Plan &p, const StepArgs &a, const void *g_out,
             if (e != cudaSuccess) return e;
         }
         gp = gprime;
+    } else if (p.adj_all) {
+        cudaError_t e = launch_params(p, sizeof(T) == 4 ? RAM_F32 : RAM_F64, a, s);
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_adj_remap_nu<T, 2>(p, a, gp, g_in, s);
-    if (e == cudaSuccess) e = launch_adj_remap_nu<T, 3>(p, a, gp, g_in, s);
-    if (e == cudaSuccess) e = launch_adj_remap_nu<T, 4>(p, a, gp, g_in, s);
+    if (p.adj_all) {
+        // limited PLM / PPM linearised at the step input
+        cudaError_t e = launch_adj_remap_nu<T, 2, true>(p, a, gp, g_in, s);
+        if (e == cudaSuccess) e = launch_adj_remap_nu<T, 3, true>(p, a, gp, g_in, s);
+        return e;
+    }
+    cudaError_t e = launch_adj_remap_nu<T, 2, false>(p, a, gp, g_in, s);
+    if (e == cudaSuccess) e = launch_adj_remap_nu<T, 3, false>(p, a, gp, g_in, s);
+    if (e == cudaSuccess) e = launch_adj_remap_nu<T, 4, false>(p, a, gp, g_in, s);
     return e;
 }
 

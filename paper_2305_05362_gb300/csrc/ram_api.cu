@@ -190,7 +190,12 @@ extern "C" ram_status ram_step_adjoint(ram_plan plan, ram_dtype dtype, const voi
     ram_status st = check_common(p, dtype, g_out, g_in);
     if (st != RAM_OK) return st;
     if (!q_in || !v0) return RAM_ERR_ARG;
-    if (p->limiter || p->a4) return RAM_ERR_UNSUPPORTED;  // the transpose: linear step, no A4
+    // the transpose of a linear step, or of a limited PLM / PPM step linearised at
+    // q_in (RAM_ADJOINT plans); no A4
+    if (p->a4 || (p->limiter && !p->adj_all)) return RAM_ERR_UNSUPPORTED;
+    if (p->limiter)
+        for (const RowInfo &ri : p->rows_h)
+            if (ri.order == 4) return RAM_ERR_UNSUPPORTED;
     if (!(dt >= 0.0) || dt > 1e300) return RAM_ERR_ARG;
     const size_t bytes = (size_t)p->n_cells * dtype_size(dtype);
     if (overlaps(q_in, g_in, bytes)) return RAM_ERR_ARG;

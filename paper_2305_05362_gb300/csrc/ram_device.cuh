@@ -236,11 +236,10 @@ __device__ __forceinline__ double shift_params(const StepArgs &a, const RowInfo 
     // fixed-point shift for rows with their own mesh: nodes are stored as fractions
     // of the period in units of 2^-64, so x - s and the periodic wrap are exact
     // integer arithmetic (uniform rows locate their edges by index instead)
-    P.sfix = 0ull;
-    if (!row.uniform) {
-        const double t = sred * row.inv_period;  // in [0, 1]
-        P.sfix = (t >= 1.0) ? 0ull : __double2ull_rn(t * 18446744073709551616.0);
-    }
+    // (uniform rows locate their edges by index; the adjoint of a limited plan
+    // locates them by position on every row)
+    const double t = sred * row.inv_period;  // in [0, 1]
+    P.sfix = (t >= 1.0) ? 0ull : __double2ull_rn(t * 18446744073709551616.0);
     double sig = sred * row.cells_per_length;
     if (sig >= (double)N) sig -= (double)N;
     const double Kd = floor(sig);

@@ -159,6 +159,9 @@ struct Plan {
     Tile *tiles_adj_nu[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int32_t adj_nu_tcap = 512;
     void *adj_scratch = nullptr;
+    // RAM_ADJOINT with the limiter on: every row (uniform ones too) has the
+    // fixed-point mesh and takes the gather adjoint, linearised at the step input
+    int32_t adj_all = 0;
     // the fourth-order cell-average correction (flag RAM_A4): scratch for the
     // corrected averages and the remapped ones, n_cells values each (FP64 size)
     int32_t a4 = 0;

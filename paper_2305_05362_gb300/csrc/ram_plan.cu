@@ -232,6 +232,9 @@ ram_status build_tiles(Plan &p)
     for (int r = 0; r < p.n_rows; ++r) {
         const RowInfo &ri = p.rows_h[r];
         const int n = ri.n;
+        if (ri.uniform && p.adj_all)
+            for (int a = 0; a < n; a += p.adj_nu_tcap)
+                p.tiles_adj_nu_h[ri.order].push_back(Tile{r, a, std::min(p.adj_nu_tcap, n - a), 0});
         if (ri.uniform) {
             const int nt = (n + p.tile_cells - 1) / p.tile_cells;
             for (int t = 0; t < nt; ++t) {
@@ -463,6 +466,7 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
     p->seg_variant = 2;
     p->seg_warps = 3;
     p->row_offset.assign(ro, ro + nr + 1);
+    p->adj_all = ((desc->flags & RAM_ADJOINT) && p->limiter) ? 1 : 0;
     const size_t n_nodes = shared ? (size_t)(ro[1] + 1) : (size_t)(ro[nr] + nr);
     p->nodes_h.assign(desc->nodes, desc->nodes + n_nodes);
 
@@ -504,13 +508,14 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
         }
         // a shared mesh serves every row, so one limited order-4 row sends them all
         ri.uniform = (row_is_uniform(x, n) && !(limited4 && (shared || ri.order == 4))) ? 1 : 0;
-        if (ri.uniform) {
+        if (ri.uniform && !p->adj_all) {
             ri.mesh_off = 0;
             ri.bucket_off = 0;
             ri.bucket_bits = 0;
             continue;
         }
-        // non-uniform row: fixed-point nodes, widths and the bucket table
+        // non-uniform row (or any row of a limited adjoint plan): fixed-point nodes,
+        // widths and the bucket table
         ri.mesh_off = (int64_t)xfix.size();
         size_t base = xfix.size();
         xfix.resize(base + n);
@@ -555,7 +560,7 @@ extern "C" ram_status ram_plan_mesh(const ram_mesh_desc *desc, int device, ram_p
             upload(&p->buckets, buckets.data(), buckets.size()) != cudaSuccess ||
             cudaMalloc((void **)&p->err, sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->row_par, sizeof(RowParams<double>) * (size_t)nr) != cudaSuccess ||
-            ((desc->flags & RAM_ADJOINT) && p->n_uniform_rows < nr &&
+            ((desc->flags & RAM_ADJOINT) && (p->n_uniform_rows < nr || p->adj_all) &&
              cudaMalloc(&p->adj_scratch, 2 * sizeof(double) * (size_t)p->n_cells) != cudaSuccess) ||
             ((desc->flags & RAM_A4) &&
              cudaMalloc(&p->a4_scratch, 2 * sizeof(double) * (size_t)p->n_cells) != cudaSuccess) ||

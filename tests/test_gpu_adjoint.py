@@ -1,6 +1,7 @@
 """GPU adjoint of the linear RAM step (limiter off, donor residual) against the FP64
 oracle's hand-derived transpose, the dot-product identity, and finite differences
-of a checkpointed rollout through torch.autograd."""
+of a checkpointed rollout through torch.autograd; the adjoint of the limited step
+linearised at its input (RAM_ADJOINT plans) against the oracle's linearisation."""
 import numpy as np
 import pytest
 
@@ -17,6 +18,10 @@ DEV = "cuda:0"
 
 def _t(a, dtype):
     return torch.tensor(np.asarray(a), dtype=dtype, device=DEV)
+
+
+def _rel(got, ref):
+    return float(np.abs(got - ref).sum() / np.abs(ref).sum())
 
 
 def _disk(n_r, n_phi, order, seed=4):
@@ -247,3 +252,147 @@ def test_rollout_gradients_nonuniform_finite_differences():
             fd = (float(f(q0 + h * eq, dv + h * ev)) - float(f(q0 - h * eq, dv - h * ev))) / (2 * h)
             an = float((gq * eq).sum() + (gdv * ev).sum())
             assert fd == pytest.approx(an, rel=1e-6, abs=1e-9 * abs(float(loss))), d
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("uniform", [True, False])
+def test_limited_adjoint_matches_the_oracle_linearisation(dtype, order, uniform):
+    """RAM_ADJOINT plans with the limiter on: the transpose of the step linearised at
+    its input (limited PLM / PPM, donor residual) against the oracle's, on uniform
+    rows (a disk) and on rows with their own mesh."""
+    lens = [40, 200, 7, 300] if not uniform else [256] * 4
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    if uniform:
+        nodes = wl.uniform_nodes(256, 0.0, 2 * np.pi)
+        plan = ram.Plan(ro, nodes, order=order, limiter=True, shared_mesh=True, adjoint=True)
+        xs = [nodes] * 4
+    else:
+        xs = [wl.random_nodes(n, seed=60 + r, ratio=3.0) for r, n in enumerate(lens)]
+        nodes = np.concatenate(xs)
+        plan = ram.Plan(ro, nodes, order=order, limiter=True, adjoint=True)
+    rng = np.random.default_rng(61 + order)
+    n = int(ro[-1])
+    # smooth rows with a few extrema each: the limiters act, away from ties
+    qh = np.concatenate([1.5 + 0.4 * wl.sine_averages(x, k=2 + r, phase=0.7 * r, period=x[-1] - x[0])
+                         + 0.2 * wl.sine_averages(x, k=5, phase=1.3 + r, period=x[-1] - x[0])
+                         for r, x in enumerate(xs)])
+    q = _t(qh, dtype)
+    g = _t(rng.standard_normal(n), dtype)
+    dt = 0.4
+    v0 = rng.uniform(-30, 30, 4) * np.array([x[-1] - x[0] for x in xs]) / np.array(lens) / dt
+    nsub = np.array([1, 2, 1, 3], dtype=np.int32)
+    dvh = np.concatenate([(rng.random(lens[r]) - 0.5) * 1.6 * nsub[r] * np.diff(xs[r]).min() / dt
+                          for r in range(4)])
+    dv = _t(dvh, dtype)
+    gin = torch.empty_like(q)
+    gdv = torch.zeros_like(dv)
+    ram.step_adjoint(plan, q, g, gin, _t(v0, torch.float64), dt, dv=dv, g_dv=gdv,
+                     nsub=_t(nsub, torch.int32))
+    torch.cuda.synchronize()
+    tol = TOL["float64" if dtype == torch.float64 else "float32"]
+    gi, gd = gin.double().cpu().numpy(), gdv.double().cpu().numpy()
+    qr, gr, dvr = q.double().cpu().numpy(), g.double().cpu().numpy(), dv.double().cpu().numpy()
+    alike = np.ones(n, dtype=bool)
+    if dtype == torch.float32:
+        # A limiter branch near a tie may be decided differently by FP32 and FP64
+        # arithmetic; there both one-sided linearisations are valid.  Compare the
+        # cells where the FP32 kernel decided as its FP64 run did (the same inputs),
+        # and require nearly all of them to be such cells.
+        g64 = torch.empty(n, dtype=torch.float64, device=DEV)
+        ram.step_adjoint(plan, q.double(), g.double(), g64, _t(v0, torch.float64), dt,
+                         dv=dv.double(), nsub=_t(nsub, torch.int32))
+        torch.cuda.synchronize()
+        g64 = g64.cpu().numpy()
+        alike = np.abs(gi - g64) <= 1e-3 * np.abs(g64).max()
+        assert alike.mean() >= 0.97, alike.mean()
+    for r in range(4):
+        sl = slice(int(ro[r]), int(ro[r + 1]))
+        ref_gi, ref_gd = oracle.step_adjoint_limited(
+            xs[r], qr[sl], gr[sl], oracle.shift_from_velocity(v0[r], dt), order, True, dvr[sl], dt,
+            int(nsub[r]))
+        m = alike[sl]
+        e1 = np.abs(gi[sl] - ref_gi)[m].sum() / np.abs(ref_gi)[m].sum()
+        assert e1 <= tol, (r, e1)
+        if dtype == torch.float64:
+            e2 = np.abs(gd[sl] - ref_gd).sum() / np.abs(ref_gd).sum()
+            assert e2 <= tol, (r, e2)
+    assert plan.check_errors() == 0
+
+
+def test_limited_adjoint_refusals():
+    n = 128
+    x = wl.uniform_nodes(n)
+    q = _t(np.ones(n), torch.float64)
+    v0 = _t([1.0], torch.float64)
+    for plan in (ram.Plan([0, n], x, order=3, limiter=True),            # no RAM_ADJOINT
+                 ram.Plan([0, n], x, order=4, limiter=True, adjoint=True)):  # limited order 4
+        with pytest.raises(ram.RamError) as e:
+            ram.step_adjoint(plan, q, q.clone(), torch.empty_like(q), v0, 0.1)
+        assert e.value.status == 7
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_limited_rollout_gradients(order):
+    """A checkpointed rollout of the limited step (FP64): the autograd gradient with
+    respect to Q0 and dv against the oracle's chain of step linearisations (its own
+    forward states, its transposes), element by element; for PLM also against
+    central differences.  The limited PPM step is piecewise smooth with many
+    branches: after a few steps some branch boundary comes within 1e-8 of the
+    state, so a central difference of any practical step straddles a kink (the
+    oracle's own differences do the same there)."""
+    w = wl.disk(n_r=8, n_phi=256, order=order, limiter=True, scheme=0, seed_dv=9, ref_n_phi=4096)
+    plan = ram.Plan.from_workload(w, adjoint=True)
+    rng = np.random.default_rng(70)
+    # rings with structure of their own (the disk's rings are flat far from the
+    # vortex, where every limiter sits on its kink); phases off the grid's symmetry,
+    # so that no two neighbouring differences tie (the nearest tie is ~1e-6 away,
+    # far beyond the 1e-8 steps below)
+    x = w.nodes
+    w.q0 = np.concatenate([w.q0[w.row_slice(r)] * (1.0 + 0.3 * wl.sine_averages(
+        x, k=2 + r % 3, phase=0.37 + 0.9 * r, period=x[-1] - x[0])) for r in range(w.n_rows)])
+    v0 = _t(w.v0, torch.float64)
+    ns = _t(w.nsub, torch.int32)
+    th = w.q0 * (1.0 + 0.05 * rng.standard_normal(w.n_cells))
+    target = _t(th, torch.float64)
+    steps = 9
+
+    def f(q0, dv):
+        return ((rollout(plan, q0, v0, w.dt, steps, dv=dv, nsub=ns, checkpoint_every=4) - target) ** 2).sum()
+
+    q0 = _t(w.q0, torch.float64).requires_grad_(True)
+    dv = _t(w.dv, torch.float64).requires_grad_(True)
+    loss = f(q0, dv)
+    gq, gdv = torch.autograd.grad(loss, (q0, dv))
+    assert plan.check_errors() == 0
+
+    # the oracle: forward states, then the transposed linearised steps in reverse
+    states = [w.q0]
+    for _ in range(steps):
+        states.append(np.concatenate([
+            oracle.step(x, states[-1][w.row_slice(r)], oracle.shift_from_velocity(w.v0[r], w.dt),
+                        order, True, w.dv[w.row_slice(r)], w.dt, 0, int(w.nsub[r]))
+            for r in range(w.n_rows)]))
+    g = 2.0 * (states[-1] - th)
+    ref_gdv = np.zeros(w.n_cells)
+    for i in reversed(range(steps)):
+        gi = np.empty_like(g)
+        for r in range(w.n_rows):
+            sl = w.row_slice(r)
+            gi[sl], gd = oracle.step_adjoint_limited(
+                x, states[i][sl], g[sl], oracle.shift_from_velocity(w.v0[r], w.dt), order, True,
+                w.dv[sl], w.dt, int(w.nsub[r]))
+            ref_gdv[sl] += gd
+        g = gi
+    assert _rel(gq.cpu().numpy(), g) <= TOL["float64"]
+    assert _rel(gdv.cpu().numpy(), ref_gdv) <= TOL["float64"]
+    if order != 2:
+        return
+    with torch.no_grad():
+        for d in range(6):
+            eq = _t(rng.standard_normal(w.n_cells), torch.float64)
+            ev = _t(rng.standard_normal(w.n_cells), torch.float64) * dv.abs().mean() * 1e-3
+            h = 1e-8
+            fd = (float(f(q0 + h * eq, dv + h * ev)) - float(f(q0 - h * eq, dv - h * ev))) / (2 * h)
+            an = float((gq * eq).sum() + (gdv * ev).sum())
+            assert fd == pytest.approx(an, rel=1e-5, abs=1e-8 * abs(float(loss))), d
