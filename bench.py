@@ -5,9 +5,12 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one full RAM step (shift by v0 dt with the PPM remap, then the
 sub-cycled van Leer residual step) of every ring of a synthetic Keplerian disk
-(1024 rings x 4096 phi cells, FP32 cells, FP64 shifts).  The inputs fit in L2,
-so L2 is flushed (a read of 2 x L2 bytes) before every timed step and the step
-time is the sum of per-step CUDA-event intervals on the launching stream.  With
+(1024 rings x 4096 phi cells, FP32 cells, FP64 shifts).  One disk's data fits
+in L2, so the timed loop steps several copies of the disk in turn (each its own
+disk advancing step by step), enough that a copy's data has left L2 before its
+next step; the K steps run back to back between one pair of CUDA events on the
+launching stream.  The same step timed on its own (L2 flushed before it, events
+around it) is reported beside it as `isolated_step`.  With
 N GPUs (torchrun, one rank per GPU) every rank advances its own disk (weak
 scaling, no data exchange); the time is the max over ranks.
 
@@ -265,6 +268,7 @@ class Runner:
                 del q_, dv_
         props = torch.cuda.get_device_properties(dev)
         l2 = int(getattr(props, "L2_cache_size", 0) or 0)
+        self.l2 = max(l2, 128 << 20)
         self.flush_buf = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
         self.flush_buf.fill_(1.0)
 
@@ -274,22 +278,80 @@ class Runner:
         dv = None if w.dv is None else torch.tensor(np.asarray(w.dv), dtype=dtype, device=self.dev)
         return q, torch.empty_like(q), dv
 
+    def n_sets(self):
+        """Copies of the workload stepped in turn, so that the data of one step has
+        left L2 (3 x L2 of algorithmic traffic in between) before its next step."""
+        per_step = self.w.n_cells * _bytes_per_cell(self.w, 4)
+        return int(min(16, max(1, math.ceil(3 * self.l2 / per_step))))
+
     def step(self, q, out, dv):
         w = self.w
         self.ram.step(self.plan, q, out, self.v0, w.dt, dv=dv, scheme=w.scheme, nsub=self.nsub)
 
+    def _hold(self, host_per_step, steps):
+        # hold the GPU while the timed loop is queued, so that the events time the
+        # kernels, not the Python launch path
+        if not self.args.no_hold:
+            self.torch.cuda._sleep(int(min(20.0, 2.0 * host_per_step * steps + 0.05) * 2.1e9))
+
     def timed(self, dtype, steps, warm):
-        torch, w = self.torch, self.w
+        """K steps back to back between one pair of CUDA events on the launching
+        stream.  The workload's R copies (n_sets) are stepped in turn, each its own
+        disk or batch advancing step by step (input and output swap), so every
+        step reads inputs that are not in L2.  Returns copy 0's state and the
+        mean time per step in ms."""
+        torch = self.torch
         import torch.distributed as dist
+        sets = [list(self.tensors(dtype)) for _ in range(self.n_sets())]
+
+        def one(k):
+            s = sets[k % len(sets)]
+            self.step(s[0], s[1], s[2])
+            s[0], s[1] = s[1], s[0]
+
+        for k in range(warm):
+            one(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(5):
+            one(warm + k)
+        host_per_step = (time.perf_counter() - t0) / 5
+        # copy 0 has taken the same number of steps in every call with the same
+        # (steps, warm): bring the counter back to a whole number of rounds
+        k0 = warm + 5
+        k0 += (-k0) % len(sets)
+        for k in range(warm + 5, k0):
+            one(k)
+        torch.cuda.synchronize()
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        self._hold(host_per_step, steps)
+        e0.record()
+        for k in range(steps):
+            one(k0 + k)
+        e1.record()
+        torch.cuda.synchronize()
+        if self.world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        q0 = sets[0][0]
+        del sets
+        return q0, ms
+
+    def timed_flushed(self, dtype, steps, warm):
+        """The step on its own: L2 flushed (a read of 2 x L2 bytes) before every
+        step and a pair of CUDA events around each step.  Per step this adds the
+        launch and drain of an isolated kernel to the step's own time."""
+        torch = self.torch
         q, out, dv = self.tensors(dtype)
         for _ in range(warm):
             self.step(q, out, dv)
             q, out = out, q
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
-        # host cost of enqueueing one timed step, so that a sleep kernel can hold
-        # the GPU until the whole timed loop is queued (the events then time the
-        # kernels, not the Python launch path)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(5):
@@ -298,28 +360,21 @@ class Runner:
             q, out = out, q
         host_per_step = (time.perf_counter() - t0) / 5
         torch.cuda.synchronize()
-        if self.world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        hold_s = min(20.0, 2.0 * host_per_step * steps + 0.05)
-        if not self.args.no_hold:
-            torch.cuda._sleep(int(hold_s * 2.1e9))
+        self._hold(host_per_step, steps)
         for k in range(steps):
-            self.flush_buf.sum()  # a read of 2 x L2 bytes evicts the step's data
+            self.flush_buf.sum()
             ev[k][0].record()
             self.step(q, out, dv)
             ev[k][1].record()
             q, out = out, q
         torch.cuda.synchronize()
-        if self.world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        return q, [a.elapsed_time(b) for a, b in ev]
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
 
     def refine_uniform(self):
-        """The autotuner times warm-cache repeats; the timed steps run on a cold L2,
-        which can rank the warp-segment launch shapes differently.  Refine them
-        under this loop's own protocol (median of 30 flushed steps each)."""
+        """The autotuner times warm-cache repeats of one step; the timed steps read
+        cold inputs back to back, which can rank the warp-segment launch shapes
+        differently.  Refine them under the timed loop's own protocol (200 steps
+        each)."""
         if self.info.n_uniform_rows != self.w.n_rows:
             return
         torch = self.torch
@@ -333,8 +388,7 @@ class Runner:
             if c is not None:
                 t.uniform_kernel_f32, t.seg_variant_f32, t.seg_warps = 1, c[0], c[1]
             self.plan.set_tuning(t)
-            _, ms_c = self.timed(torch.float32, 30, 3)
-            med = statistics.median(ms_c)
+            _, med = self.timed(torch.float32, 200, 3)
             if med < best_ms:
                 best, best_ms = c, med
         t = self.plan.tuning()
@@ -380,7 +434,7 @@ class Runner:
         clocks = sampler.stop() if rank == 0 else None
         st = self.plan.check_errors()
         from paper_2305_05362_gb300 import shard
-        total_s = sum(ms32) / 1e3
+        total_s = ms32 * steps / 1e3
         total_max = shard.global_max(total_s)
         value = w.n_cells * world * steps / total_max / 1e9
         bpc = _bytes_per_cell(w, 4)
@@ -398,15 +452,25 @@ class Runner:
                             "peak_kind": peak_kind, "bytes_per_cell": bpc,
                             "traffic": None if tr is None else tr["dram_bytes_per_launch"]},
                "clocks": clocks, "device_status": st, "tuning": tuning,
-               "l2": "read of 2x L2 before every timed step; step time = sum of per-step "
-                     "CUDA-event intervals"}
+               "l2": "inputs larger than L2: %d copies of the workload stepped in turn "
+                     "(%.0f MB of step traffic between two steps of one copy); the K steps "
+                     "back to back between one pair of CUDA events"
+                     % (self.n_sets(), (self.n_sets() - 1) * w.n_cells * bpc / 1e6)}
+        # the same step on its own, L2 flushed before it: an isolated launch
+        fl_ms = self.timed_flushed(torch.float32, 50, 3)
+        rec["isolated_step"] = {
+            "ms_per_step": fl_ms, "value": w.n_cells * world / (fl_ms / 1e3) / 1e9,
+            "unit": UNIT, "roofline_frac": w.n_cells * bpc / (fl_ms / 1e3) / 1e9 / peak,
+            "protocol": "L2 flushed (read of 2x L2) before each step, CUDA events around "
+                        "each step, median of 50: adds an isolated kernel's launch and "
+                        "drain to every step"}
         if with_fp64:
             n64 = min(fp64_steps, steps)
             q64, ms64 = self.timed(torch.float64, n64, 3)
             q32b, _ = self.timed(torch.float32, n64, 3)
             a, b = q32b.double(), q64
             rec["fp64_same_launch"] = {
-                "value": w.n_cells * n64 / (sum(ms64) / 1e3) / 1e9, "unit": UNIT, "steps": n64,
+                "value": w.n_cells * n64 / (ms64 * n64 / 1e3) / 1e9, "unit": UNIT, "steps": n64,
                 "form": "the same step in FP64 (cells and arithmetic), autotuned",
                 "rel_l1_fp32_vs_fp64": float((a - b).abs().sum() / b.abs().sum())}
             del q64, q32b
@@ -588,6 +652,7 @@ def main():
                        "tuning": head["tuning"]},
             "gpu_launches": head["gpu_launches"],
             "roofline": head["roofline"],
+            "isolated_step": head.get("isolated_step"),
             "fp64_single": head.get("fp64_same_launch"),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": head["clocks"],
             "device_status": head["device_status"],

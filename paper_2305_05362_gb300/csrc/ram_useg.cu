@@ -430,10 +430,13 @@ struct RingLayout {
 // stages filled by asynchronous 16-byte copies (the data does not pass through
 // registers until the segment is computed), so that S segments per warp are in
 // flight.  A warp reads a stage into registers, refills it at once with the
-// copies of its segment S ahead and computes.  The row's shift parameters are
-// formed in the kernel (shift_params_two_float), so no parameter kernel runs
-// before it when every row of the step takes this kernel; the phase is then
-// advanced here too (a.row_phase).  FP32 rows of at least 32 V + 12 cells.
+// copies of its next segment and computes.  The warps of a row take its segments
+// from a counter in shared memory as they issue the copies, so a warp on a
+// crowded scheduler takes fewer of them and the row's CTA finishes with its
+// warps.  The row's shift parameters are formed in the kernel
+// (shift_params_two_float), so no parameter kernel runs before it when every row
+// of the step takes this kernel; the phase is then advanced here too
+// (a.row_phase).  FP32 rows of at least 32 V + 12 cells.
 template <int ORDER, int V, bool LIM, bool VL>
 __global__ void __launch_bounds__(256, 3)
     k_useg_ring(StepArgs a, const int32_t *row_ids)
@@ -441,13 +444,16 @@ __global__ void __launch_bounds__(256, 3)
     using L = RingLayout<V>;
     constexpr int VEC = 4, NW = V + 12;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int seg_next;                // the row's next segment to hand out
+    __shared__ int seg_slot[8][L::S];       // segment held by each warp's stages
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
     float *ring = reinterpret_cast<float *>(smem_raw + (size_t)warp * L::warp_bytes);
+    int *slot = seg_slot[warp];
 
     const bool has_dv = (a.mode != MODE_SHIFT) && (a.dv != nullptr);
     const int r = row_ids[blockIdx.x];
     const RowInfo row = a.rows[r];  // plan data: readable before the previous kernel ends
+    if (threadIdx.x == 0) seg_next = 0;
     pdl_wait();
     // every warp forms the row's shift parameters itself, in two-float arithmetic
     // (no FP64 instruction, no parameter kernel before this one)
@@ -470,21 +476,26 @@ __global__ void __launch_bounds__(256, 3)
     float *qout = static_cast<float *>(a.q_out) + P.cell_off;
     const int off = ((-P.K - 1) % VEC + VEC) % VEC;
     const bool use_dv = has_dv && nsub > 0;
-    const int nmine = warp < nseg ? (nseg - warp + nwarps - 1) / nwarps : 0;
+    __syncthreads();  // seg_next is set
 
-    // copies of this warp's i-th segment into stage i % S, one commit group per
-    // segment (empty past the warp's last one, so that group i is always the
-    // (i+1)-th).  The window starts at the 16-byte aligned cell wb in [0, N); a
-    // vector past the row's end comes from its start.  Lane l copies the 16-byte
-    // chunks l, l + 32, ... of the window and of the dv range.
+    // copies of the segment this warp takes next into stage i % S, one commit
+    // group per stage use (empty once the row's segments are all handed out, so
+    // that group i is always the (i+1)-th).  The window starts at the 16-byte
+    // aligned cell wb in [0, N); a vector past the row's end comes from its
+    // start.  Lane l copies the 16-byte chunks l, l + 32, ... of the window and
+    // of the dv range.
     const uint32_t ring_s = smem_u32(ring) + 16u * lane;
     constexpr uint32_t kStageBytes = L::stage_floats * 4;
     const int wshift = P.K + 1 + off + VEC;  // window start = w0 - wshift
     const float *const qlane = qin + 4 * lane;
     const float *const dlane = use_dv ? dvp + 4 * lane : nullptr;
-    auto issue = [=](int i) {
-        if (i < nmine) {
-            const int w0 = (warp + i * nwarps) * stride - H4;
+    auto issue = [&](int i) {
+        int seg = 0;
+        if (lane == 0) seg = atomicAdd(&seg_next, 1);
+        seg = __shfl_sync(0xffffffffu, seg, 0);
+        slot[i % L::S] = seg;  // every lane writes the same value
+        if (seg < nseg) {
+            const int w0 = seg * stride - H4;
             const uint32_t sq = ring_s + (uint32_t)(i % L::S) * kStageBytes;
             const int wb = wrap2(w0 - wshift, N);
             if (wb + L::WQ <= N) {
@@ -521,7 +532,11 @@ __global__ void __launch_bounds__(256, 3)
     float cmax = 0.0f;
     // this lane's cells in a stage: window floats lane V .., dv floats WQ + lane V ..
     const uint32_t lds0 = smem_u32(ring) + 4u * V * lane;
-    for (int i = 0; i < nmine; ++i) {
+    for (int i = 0;; ++i) {
+        // the stages are used in the order they were filled: once a stage holds no
+        // segment, no later one does
+        const int seg = slot[i % L::S];
+        if (seg >= nseg) break;
         // S + i groups committed; segment i's is complete once at most S - 1 remain
         cp_async_wait<L::S - 1>();
         __syncwarp();
@@ -533,11 +548,11 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
             for (int c = 0; c < V / VEC; ++c) xv[c] = lds128(sq + L::WQ * 4 + 16u * c);
         }
-        // every lane has read the stage: refill it with the segment S ahead
+        // every lane has read the stage: refill it with the warp's next segment
         __syncwarp();
         issue(i + L::S);
-        seg_compute_f32<ORDER, V, LIM, VL>(P, N, nsub, H4, stride, off, use_dv,
-                                           warp + i * nwarps, lane, xw, xv, qout, cmax);
+        seg_compute_f32<ORDER, V, LIM, VL>(P, N, nsub, H4, stride, off, use_dv, seg, lane, xw,
+                                           xv, qout, cmax);
     }
     cp_async_wait<0>();
     if (cmax > 1.0f) atomicOr(a.err, ERR_CFL);
@@ -581,9 +596,10 @@ cudaError_t launch_ring_k(const Plan &p, const StepArgs &a, cudaStream_t s, int 
     static bool configured[64] = {false};
     const int dev = p.device < 64 ? p.device : 63;
     if (!configured[dev]) {
+        // the most any launch asks for (8 warps); the kernel's static arrays come on top
         cudaError_t e = cudaFuncSetAttribute(k_useg_ring<ORDER, V, LIM, VL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(227 * 1024));
+                                             8 * RingLayout<V>::warp_bytes);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
