@@ -676,6 +676,10 @@ cudaError_t launch_general_class(const Plan &p, const GenList &gl, const StepArg
 
 // Whole-row tiles (short rows) and windowed tiles run as two launches, each with
 // the shared memory of its own largest tile (plan-time sizes).
+// output cells per lane of k_gwarp (FP32: three amortise a lane's bucket lookup
+// and loads better than two; measured on the 512-row batch)
+template <typename T> constexpr int kGwarpV = sizeof(T) == 4 ? 3 : 2;
+
 template <typename T, int ORDER>
 cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, int &launched)
 {
@@ -688,7 +692,7 @@ cudaError_t launch_general_t(const Plan &p, const StepArgs &a0, cudaStream_t s, 
         a.tiles = gl.tiles;
         a.n_tiles = n;
         const int threads = p.threads < 512 ? p.threads : 512;
-        cudaError_t e = launch_pdl(k_gwarp<T, ORDER, 2>, n, threads, 0, s, a,
+        cudaError_t e = launch_pdl(k_gwarp<T, ORDER, kGwarpV<T>>, n, threads, 0, s, a,
                                    launched == 0 ? 1 : 0,
                                    static_cast<const RowParams<T> *>(p.row_par));
         if (e == cudaSuccess) ++launched;
