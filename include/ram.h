@@ -250,10 +250,11 @@ typedef struct {
     int32_t seg_variant_f32;            /* warp-segment kernel, FP32: 0 = one segment in
                                            flight per warp, 1 = the loads of a warp's next
                                            segment in flight while it computes, 2 = a ring
-                                           of 4 shared-memory stages per warp, the row's
-                                           shift parameters formed in the kernel (no
-                                           parameter kernel when every row takes it;
-                                           the default) */
+                                           of 2 shared-memory stages per warp, the row's
+                                           segments handed out by a counter as the warps
+                                           issue their copies, its shift parameters
+                                           formed in the kernel (no parameter kernel
+                                           when every row takes it; the default) */
     int32_t seg_warps;                  /* warp-segment kernel: warps per row CTA, 3..8
                                            (default 3) */
     int32_t nonuniform_kernel_f32;      /* FP32 rows with their own mesh: 0 = the
