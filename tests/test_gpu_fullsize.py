@@ -1,8 +1,8 @@
 """GPU parity at the benchmark's full sizes, in the launch configurations the
 benchmark times, on sampled rows that the FP64 oracle computes one by one:
 
-  - the batched recipe: 512 uneven rows of 64..65536 cells with their own
-    non-uniform meshes, per-row shifts of 0.3-200 mean cells, orders 2/3/4,
+  - the batched recipe: 512 and 8192 uneven rows of 64..65536 cells with their
+    own non-uniform meshes, per-row shifts of 0.3-200 mean cells, orders 2/3/4,
     launch shapes chosen by the autotuner;
   - the large disk: 8192 rings x 16384 cells (134 M cells), PPM + van Leer
     residual, in both warp-count shapes the benchmark picks between.
@@ -73,6 +73,30 @@ def test_batched_512_rows_autotuned(batched_512, dtype, nseg):
         ref = oracle.step(w.row_nodes(r), q64[sl], oracle.shift_from_velocity(w.v0[r], w.dt),
                           int(w.order[r]), w.limiter)
         assert _rel(got[sl], ref) <= TOL[dtype], (r, int(w.order[r]), _rel(got[sl], ref))
+
+
+def test_batched_8192_rows_autotuned_sampled():
+    """The 8192-row batch the benchmark times (76 M cells, rows of 64-65536 cells
+    with their own meshes, orders 2/3/4), FP32, in the autotuner's launch shapes:
+    sampled rows against the oracle."""
+    w = wl.batched(n_rows=8192)
+    assert w.n_cells > 70_000_000
+    plan = ram.Plan.from_workload(w)
+    q = _t(w.q0, torch.float32)
+    out = torch.empty_like(q)
+    v0 = _t(w.v0, torch.float64)
+    ram.autotune(plan, q, out, v0, w.dt, reps=2)
+    ram.step(plan, q, out, v0, w.dt)
+    torch.cuda.synchronize()
+    assert plan.check_errors() == 0
+    q64 = q.double().cpu().numpy()
+    for r in _sample_rows(w, 24, seed=2):
+        sl = w.row_slice(r)
+        got = out[sl].double().cpu().numpy()
+        ref = oracle.step(w.row_nodes(r), q64[sl], oracle.shift_from_velocity(w.v0[r], w.dt),
+                          int(w.order[r]), w.limiter)
+        assert _rel(got, ref) <= TOL["float32"], (r, int(w.order[r]), _rel(got, ref))
+    del plan
 
 
 def test_large_disk_sampled_rings():
