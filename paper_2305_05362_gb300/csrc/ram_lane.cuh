@@ -207,7 +207,9 @@ __device__ __forceinline__ void residual_group(const T (&z)[V + 4], const T (&v)
 // lane forms the half slopes of its own cells and the fluxes of its own faces;
 // the neighbour cells and slope on the left and the flux on the right come from
 // the adjacent lanes by shuffles, so no slope or flux is formed twice.  The
-// flux is the one of residual_group; lanes 0 and 31 take their outer
+// flux is the one of residual_group, written with the upwind cell selected by
+// the sign of c: F = c (Q_up + (1 - |c|) h_up), h_up the upwind half slope
+// taken toward the face; lanes 0 and 31 take their outer
 // neighbours from the other end of the warp, which spoils the outermost two
 // cells of the warp's range per van Leer sub-step (one per donor sub-step):
 // the caller keeps them as halo.
@@ -230,14 +232,12 @@ __device__ __forceinline__ void residual_warp(float (&cur)[V], const float (&c)[
         const float hl = __shfl_up_sync(full, h[V - 1], 1);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            const float ap = fmaxf(c[k], 0.0f);
-            const float am = c[k] - ap;
-            const float zk1 = k ? cur[k - 1] : zl;
-            const float hk1 = k ? h[k - 1] : hl;
-            const float f = fmaf(ap, zk1, am * cur[k]);
-            const float wp = fmaf(-ap, ap, ap);   // c+ (1 - c+)
-            const float wm = fmaf(-am, am, -am);  // -c- (1 + c-)
-            F[k] = fmaf(wp, hk1, fmaf(wm, h[k], f));
+            // the upwind cell's value and half slope (the left cell for c > 0, the
+            // right one, slope negated, otherwise): F = c (Q_up + (1 - |c|) h_up)
+            const bool pos = c[k] > 0.0f;
+            const float zu = pos ? (k ? cur[k - 1] : zl) : cur[k];
+            const float hu = pos ? (k ? h[k - 1] : hl) : -h[k];
+            F[k] = c[k] * fmaf(1.0f - fabsf(c[k]), hu, zu);
         }
     } else {
 #pragma unroll
