@@ -60,18 +60,27 @@ def _workload(name, rank, disk=None):
         return wl.batched(n_rows=512, seed_len=6 + 100 * rank)
     if name == "batched_large":
         return wl.batched(n_rows=8192, seed_len=6 + 100 * rank)
+    if name == "batched_dv":
+        return wl.batched(n_rows=512, seed_len=6 + 100 * rank, with_dv=True)
+    if name == "line":
+        return wl.line_nonuniform()
     raise SystemExit("unknown workload %s" % name)
 
 
 def _bytes_per_cell(w, es):
     """Algorithmic bytes of one step per cell: read Q, write Q, read dv when the
-    residual step runs, and read the row's own mesh (one 8-byte node per cell)
-    when the rows do not share one."""
+    residual step runs, and read the mesh (one 8-byte node per mesh cell) when it
+    is not uniform: every row's own mesh, or one shared non-uniform mesh once."""
     b = 2 * es
     if w.dv is not None:
         b += es
     if not w.shared_mesh:
         b += 8
+    else:
+        x = np.asarray(w.row_nodes(0), dtype=np.float64)
+        dx = np.diff(x)
+        if not np.allclose(dx, dx.mean(), rtol=1e-12, atol=0.0):
+            b += 8.0 * dx.size / w.n_cells
     return b
 
 
@@ -244,7 +253,8 @@ def _dominant_kernel(info, w, tuning):
 
 class Runner:
     """One workload on this rank's GPU: its plan, device tensors and the timed
-    loop (CUDA events on the launching stream, L2 flushed before every step)."""
+    loop (CUDA events on the launching stream; copies of the workload stepped in
+    turn so that every step reads inputs that are not in L2)."""
 
     def __init__(self, w, dev, world, args, tuning=None, autotune=True):
         import torch
@@ -430,7 +440,15 @@ class Runner:
         sampler = ClockSampler(_uuid(self.dev) if rank == 0 else None)
         if rank == 0:
             sampler.start()
-        q32, ms32 = self.timed(torch.float32, steps, warmup)
+        per_step = w.n_cells * _bytes_per_cell(w, 4)
+        small = self.n_sets() * per_step < 2 * self.l2
+        if small:
+            # copies of a workload this small cannot leave L2 between their steps:
+            # each step is timed on its own after an L2 flush instead
+            q32 = None
+            ms32 = self.timed_flushed(torch.float32, steps, warmup)
+        else:
+            q32, ms32 = self.timed(torch.float32, steps, warmup)
         clocks = sampler.stop() if rank == 0 else None
         st = self.plan.check_errors()
         from paper_2305_05362_gb300 import shard
@@ -452,10 +470,13 @@ class Runner:
                             "peak_kind": peak_kind, "bytes_per_cell": bpc,
                             "traffic": None if tr is None else tr["dram_bytes_per_launch"]},
                "clocks": clocks, "device_status": st, "tuning": tuning,
-               "l2": "inputs larger than L2: %d copies of the workload stepped in turn "
-                     "(%.0f MB of step traffic between two steps of one copy); the K steps "
-                     "back to back between one pair of CUDA events"
-                     % (self.n_sets(), (self.n_sets() - 1) * w.n_cells * bpc / 1e6)}
+               "l2": ("L2 flushed (read of 2x L2) before each step, CUDA events around "
+                      "each step, median of the steps: the workload is too small for "
+                      "copies of it to exceed L2" if small else
+                      "inputs larger than L2: %d copies of the workload stepped in turn "
+                      "(%.0f MB of step traffic between two steps of one copy); the K steps "
+                      "back to back between one pair of CUDA events"
+                      % (self.n_sets(), (self.n_sets() - 1) * w.n_cells * bpc / 1e6))}
         # the same step on its own, L2 flushed before it: an isolated launch
         fl_ms = self.timed_flushed(torch.float32, 50, 3)
         rec["isolated_step"] = {
@@ -468,6 +489,8 @@ class Runner:
             n64 = min(fp64_steps, steps)
             q64, ms64 = self.timed(torch.float64, n64, 3)
             q32b, _ = self.timed(torch.float32, n64, 3)
+            if small:
+                ms64 = self.timed_flushed(torch.float64, n64, 3)
             a, b = q32b.double(), q64
             rec["fp64_same_launch"] = {
                 "value": w.n_cells * n64 / (ms64 * n64 / 1e3) / 1e9, "unit": UNIT, "steps": n64,
@@ -537,7 +560,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="disk", choices=["disk", "disk_large", "batched", "batched_large"])
+    ap.add_argument("--workload", default="disk",
+                    choices=["disk", "disk_large", "batched", "batched_large", "batched_dv", "line"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
@@ -619,6 +643,8 @@ def main():
     if not args.no_extra and args.workload == "disk" and disk is None:
         for key, name, steps in (("batched", "batched", 2000),
                                  ("batched_large", "batched_large", 300),
+                                 ("batched_dv", "batched_dv", 1000),
+                                 ("line_nonuniform", "line", 200),
                                  ("roofline_R", "disk_large", 1000)):
             wx = _workload(name, rank)
             rx = Runner(wx, dev, world, args)
@@ -629,7 +655,7 @@ def main():
             rx.close()
             del rx
             torch.cuda.empty_cache()
-            if key == "batched" and world == 1:
+            if key in ("batched", "batched_dv") and world == 1:
                 rec["fp64_single_problem"] = fp64_single_problem(wx, dev)
             extra[key] = rec
             del wx

@@ -211,9 +211,11 @@ def disk(n_r: int = 1024, n_phi: int = 4096, seed_dv: int = 4, steps: int = 500,
 def batched(n_rows: int = 512, n_min: int = 64, n_max: int = 65536, seed_len: int = 6,
             seed_mesh0: int = 7, seed_shift: int = 9, seed_order: int = 10,
             seed_q0: int = 11, steps: int = 200, orders=(2, 3, 4),
-            limiter: bool = False) -> Workload:
+            limiter: bool = False, with_dv: bool = False, seed_dv: int = 12) -> Workload:
     """Uneven independent rows, each with its own non-uniform mesh of length 1,
-    shift exp(U[ln 0.3, ln 200]) mean cells per step, order drawn from `orders`."""
+    shift exp(U[ln 0.3, ln 200]) mean cells per step, order drawn from `orders`.
+    with_dv: a residual velocity at the interfaces, 0.3 dx_min sin(2 pi (3 x + phi_r))
+    / dt on row r (phi_r seeded), so its Courant number stays below 0.3; van Leer."""
     rng = np.random.default_rng(seed_len)
     lens = np.round(np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_rows)))
     lens = lens.astype(np.int64)
@@ -231,9 +233,18 @@ def batched(n_rows: int = 512, n_min: int = 64, n_max: int = 65536, seed_len: in
     v0 = shift_cells / lens / dt  # every row has length 1
     ro_ = np.random.default_rng(seed_order)
     order = ro_.choice(np.array(orders, dtype=np.int8), size=n_rows)
-    return Workload("batched_%d_rows" % n_rows, ro, nodes, False, order, limiter, q0,
-                    v0, dt, None, 1, np.ones(n_rows, dtype=np.int32), steps,
-                    "uneven rows %d..%d cells" % (n_min, n_max))
+    dv = None
+    if with_dv:
+        dv = np.empty(int(ro[-1]), dtype=np.float64)
+        ph = np.random.default_rng(seed_dv).random(n_rows)
+        for rr in range(n_rows):
+            x = nodes[ro[rr] + rr: ro[rr + 1] + rr + 1]
+            amp = 0.3 * float(np.diff(x).min()) / dt
+            dv[ro[rr]:ro[rr + 1]] = amp * np.sin(2.0 * math.pi * (3.0 * x[:-1] + ph[rr]))
+    return Workload("batched_%d_rows%s" % (n_rows, "_dv" if with_dv else ""), ro, nodes, False,
+                    order, limiter, q0, v0, dt, dv, 1, np.ones(n_rows, dtype=np.int32), steps,
+                    "uneven rows %d..%d cells%s" % (n_min, n_max,
+                                                    ", van Leer residual" if with_dv else ""))
 
 
 # --------------------------------------------------------------------------
