@@ -50,7 +50,10 @@ constexpr int kCover = kStride + 32 * kV;    // cells the two chunks cover (252)
 constexpr int kWcap = kCover - 2;            // window cells a warp can hold (250)
 constexpr int kEmax = kNseg + 2 * kGenHalo;  // extended segment (residual halo)
 
-constexpr int kSkewed = kCover + 4;  // length of the per-window arrays (kCover + 1 nodes)
+constexpr int kSkewed = kCover + 4 + (kCover + 4) / 32 + 1;  // padded length of the per-window arrays
+// window index -> padded index: one word after every 32, so that lanes storing
+// cells 4 apart hit 32 different banks
+__device__ __forceinline__ int pz(int s) { return s + (s >> 5); }
 
 // Per-warp shared-memory layout (32-bit words).
 struct NLayout {
@@ -255,12 +258,13 @@ __device__ __forceinline__ float eval_G(const float *c, int w, float xi)
     const int s = w;
     float g;
     if (ORDER == 2) {
-        g = fmaf(xi, c[kSkewed + s], c[s]);
+        g = fmaf(xi, c[kSkewed + pz(s)], c[pz(s)]);
     } else if (ORDER == 3) {
-        g = fmaf(xi, fmaf(xi, c[2 * kSkewed + s], c[kSkewed + s]), c[s]);
+        g = fmaf(xi, fmaf(xi, c[2 * kSkewed + pz(s)], c[kSkewed + pz(s)]), c[pz(s)]);
     } else {
-        g = fmaf(xi, fmaf(xi, fmaf(xi, c[3 * kSkewed + s], c[2 * kSkewed + s]), c[kSkewed + s]),
-                 c[s]);
+        g = fmaf(xi, fmaf(xi, fmaf(xi, c[3 * kSkewed + pz(s)], c[2 * kSkewed + pz(s)]),
+                          c[kSkewed + pz(s)]),
+                 c[pz(s)]);
     }
     return xi * g;
 }
@@ -455,17 +459,17 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
 #pragma unroll
         for (int i = 0; i < kV; ++i) {
             const int s = sb + i;
-            sR[s] = r[i];
-            sQ[s] = q[i];
-            sH[s] = h[i];
-            sIW[s] = rcp_approx((float)(r[i + 1] - r[i]));
+            sR[pz(s)] = r[i];
+            sQ[pz(s)] = q[i];
+            sH[pz(s)] = h[i];
+            sIW[pz(s)] = rcp_approx((float)(r[i + 1] - r[i]));
             const int wl = lane * kV + i;  // cell within the chunk
             if (wl >= lo && wl < kStride + 2) {
 #pragma unroll
-                for (int k = 0; k < ORDER; ++k) sC[k * kSkewed + s] = b[i][k];
+                for (int k = 0; k < ORDER; ++k) sC[k * kSkewed + pz(s)] = b[i][k];
             }
         }
-        if (lane == 31) sR[w0 + kV] = r[kV];  // the chunk's last node
+        if (lane == 31) sR[pz(w0 + kV)] = r[kV];  // the chunk's last node
     }
     __syncwarp();
 
@@ -501,19 +505,19 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
 #pragma unroll
                 for (int step = 128; step > 0; step >>= 1) {
                     const int m = w + step;
-                    if (m < hiw && sR[m] <= ry) w = m;
+                    if (m < hiw && sR[pz(m)] <= ry) w = m;
                 }
             } else {
                 // a walk: mostly zero, one or two nodes
-                if (w + 1 < hiw && sR[w + 1] <= ry) {
+                if (w + 1 < hiw && sR[pz(w + 1)] <= ry) {
                     ++w;
-                    while (w + 1 < hiw && sR[w + 1] <= ry) ++w;
+                    while (w + 1 < hiw && sR[pz(w + 1)] <= ry) ++w;
                 }
             }
-            const uint32_t d = ry - sR[w];
+            const uint32_t d = ry - sR[pz(w)];
             we[e] = w;
             de[e] = d;
-            G[e] = eval_G<ORDER>(sC, w, (float)d * sIW[w]);
+            G[e] = eval_G<ORDER>(sC, w, (float)d * sIW[pz(w)]);
         }
 #pragma unroll
         for (int e = 0; e < kVE; ++e) {
@@ -523,11 +527,11 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
             // in between and the start of cell wr
             float mass = G[e + 1] - G[e];
             if (wr != wl) {
-                mass += sQ[wl] * sH[wl];
-                for (int m = wl + 1; m < wr; ++m) mass += sQ[m] * sH[m];
+                mass += sQ[pz(wl)] * sH[pz(wl)];
+                for (int m = wl + 1; m < wr; ++m) mass += sQ[pz(m)] * sH[pz(m)];
             }
             // both edges on the nodes of one source cell: its value unchanged
-            const float val = ((de[e] | de[e + 1]) == 0 && wr == wl + 1) ? sQ[wl]
+            const float val = ((de[e] | de[e + 1]) == 0 && wr == wl + 1) ? sQ[pz(wl)]
                                                                          : mass * rcp_approx(wo);
             if (j0 + e < ne) {
                 if (RESID) {
