@@ -57,7 +57,7 @@ __device__ __forceinline__ int pz(int s) { return s + (s >> 5); }
 
 // Per-warp shared-memory layout (32-bit words).
 struct NLayout {
-    int r, q, h, iw, c, p, p2, wo, v, f, total;
+    int r, q, h, iw, c, p, total;
 };
 
 __host__ __device__ inline NLayout nseg_layout(bool resid)
@@ -73,12 +73,10 @@ __host__ __device__ inline NLayout nseg_layout(bool resid)
     L.q = put(kSkewed);       // window cell values
     L.h = put(kSkewed);       // window cell widths (mean-width units)
     L.iw = put(kSkewed);      // 1 / width in position units
-    L.c = put(4 * kSkewed);   // cumulative coefficients, 4 arrays
-    L.p = put(resid ? kEmax : 0);
-    L.p2 = put(resid ? kEmax : 0);
-    L.wo = put(resid ? kEmax : 0);
-    L.v = put(resid ? kEmax + 1 : 0);
-    L.f = put(resid ? kEmax + 1 : 0);
+    // cumulative coefficients, 4 arrays; once the edges are done, the residual's
+    // output widths, second state, velocities and fluxes in their place
+    L.c = put(4 * kSkewed);
+    L.p = put(resid ? kEmax : 0);  // the remapped segment, the residual's first state
     L.total = o;
     return L;
 }
@@ -473,11 +471,8 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
     }
     __syncwarp();
 
-    float *sP = nullptr, *sWo = nullptr;
-    if (RESID) {
-        sP = reinterpret_cast<float *>(base) + Lo.p;
-        sWo = reinterpret_cast<float *>(base) + Lo.wo;
-    }
+    float *sP = nullptr;
+    if (RESID) sP = reinterpret_cast<float *>(base) + Lo.p;
     // ---- shifted edges and output masses (Eqs. 16, 18, 26) ----
     const uint64_t off = g.S + xA;  // window-relative position of a shifted node: x - off
     const int hiw = W - kHR;        // node after the last edge cell
@@ -536,7 +531,6 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
             if (j0 + e < ne) {
                 if (RESID) {
                     sP[j0 + e] = val;
-                    sWo[j0 + e] = wo;
                 } else {
                     g.qout[i0 + j0 + e] = val;
                 }
@@ -545,9 +539,12 @@ __device__ __forceinline__ void nseg_segment(const SegCtx &g, unsigned char *bas
     }
     if (RESID) {
         // ---- residual sub-steps (Eq. 6) on the extended segment ----
-        float *sP2 = reinterpret_cast<float *>(base) + Lo.p2;
-        float *sV = reinterpret_cast<float *>(base) + Lo.v;
-        float *sF = reinterpret_cast<float *>(base) + Lo.f;
+        // the coefficient arrays are free once every lane has left the edges
+        __syncwarp();
+        float *sWo = sC, *sP2 = sC + kSkewed, *sV = sC + 2 * kSkewed, *sF = sC + 3 * kSkewed;
+        static_assert(kSkewed >= kEmax + 1, "the residual's arrays fit the coefficient arrays");
+        for (int j = lane; j < ne; j += 32)
+            sWo[j] = (float)(g.X[wrap3(a0 + j + 1, N)] - g.X[wrap3(a0 + j, N)]) * g.scale;
         for (int j = lane; j <= ne; j += 32) sV[j] = g.dvp[wrap3(a0 + j, N)];
         __syncwarp();
         const int R = g.R;
