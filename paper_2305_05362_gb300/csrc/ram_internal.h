@@ -75,7 +75,7 @@ constexpr int kNsegV = 4;
 constexpr int kNseg = 96;
 constexpr int kNsegHR = 2;          // reconstruction halo, cells per side
 constexpr int kNsegWarps = 8;
-constexpr int kNsegPerWarp = 2;
+constexpr int kNsegPerWarp = 4;
 // shortest row it takes (a segment and its residual halo span less than a period)
 constexpr int kNsegMinCells = 2 * kGenHalo + 2;
 
