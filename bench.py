@@ -79,7 +79,7 @@ def _bytes_per_cell(w, es):
     else:
         x = np.asarray(w.row_nodes(0), dtype=np.float64)
         dx = np.diff(x)
-        if not np.allclose(dx, dx.mean(), rtol=1e-12, atol=0.0):
+        if not np.allclose(dx, dx.mean(), rtol=1e-9, atol=0.0):
             b += 8.0 * dx.size / w.n_cells
     return b
 
